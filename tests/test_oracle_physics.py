@@ -1,0 +1,178 @@
+"""Whole-step pins of the oracle against closed-form flows and the paper's claims:
+decay of exact Navier-Stokes solutions at the viscosity of Eq. 53, isotropy of
+that viscosity on cuboid lattices once the corrections of Eq. 30/38-40 are on,
+the rectangular-duct series (Eq. 70), the moving-lid bounce-back of Eq. 69, the
+local strain-rate recovery of Eq. 44-49, and global conservation.  CPU only."""
+import numpy as np
+import pytest
+
+import synth
+from tests.analytic import duct_series, fit_decay_rate, lid_bounce_coefficients_eq69
+
+
+def _proj(u, u0):
+    return float((u * u0).sum() / (u0 * u0).sum())
+
+
+def _decay(o, rho, u, steps, every):
+    f = o.init(rho, u)
+    ts, amps = [], []
+    for t in range(0, steps + 1, every):
+        if t:
+            f = o.run(f, every)
+        _, uu = o.moments(f)
+        ts.append(t)
+        amps.append(_proj(uu, u))
+    return ts, amps
+
+
+def _make(oracle_mod, n, r, s, cs2, nu, corr="LOCAL", **kw):
+    wn, _ = oracle_mod.omega_from_viscosity(nu, cs2 / 3, cs2)
+    return oracle_mod.Oracle(*n, r=r, s=s, cs2=cs2, omega_nu=wn, omega_xi=1.0,
+                             corr=getattr(oracle_mod, "CORR_" + corr), **kw)
+
+
+@pytest.mark.parametrize("r,s,cs2,nu,n,fa,ga", [
+    (1.0, 0.5, 1 / 12, 0.05, (1, 1, 32), 0, 2),
+    (0.5, 2.0, 1 / 12, 0.02, (16, 32, 4), 2, 1),
+    (0.25, 1.0, 1 / 48, 0.005, (1, 64, 1), 0, 1),
+])
+def test_shear_wave_decays_at_eq53_viscosity(oracle_mod, r, s, cs2, nu, n, fa, ga):
+    """A plane shear wave is an exact NS solution decaying as exp(-nu k^2 t)."""
+    o = _make(oracle_mod, n, r, s, cs2, nu)
+    rho, u, k2 = synth.shear_wave(*n, r, s, 1e-3, fa, ga)
+    ts, amps = _decay(o, rho, u, 400, 40)
+    assert fit_decay_rate(ts[1:], amps[1:]) / (k2 * nu) == pytest.approx(1.0, abs=5e-3)
+
+
+@pytest.mark.parametrize("r,s,plane,n", [
+    (1.0, 0.5, "xy", (16, 16, 1)), (1.0, 0.5, "xz", (16, 1, 32)), (1.0, 0.5, "yz", (1, 16, 32)),
+    (0.5, 0.5, "xy", (16, 32, 1)), (0.5, 0.5, "xz", (16, 1, 32)),
+])
+def test_corrections_make_viscosity_isotropic(oracle_mod, r, s, plane, n):
+    """Plane Taylor-Green vortices (exact NS solutions, decay exp(-nu |k|^2 t)) in every
+    coordinate plane of a cuboid lattice: with the corrections the effective viscosity
+    equals Eq. 53 in every plane; without them the normal-stress errors E_js of Eq. 22
+    bias it wherever (3 cs2 - c_i^2) != 0."""
+    cs2, nu = 1 / 12, 0.02
+    rates = {}
+    for corr in ("LOCAL", "NONE"):
+        o = _make(oracle_mod, n, r, s, cs2, nu, corr)
+        rho, u, k2 = synth.taylor_green_2d(*n, r, s, 1e-3, plane)
+        ts, amps = _decay(o, rho, u, 300, 30)
+        rates[corr] = fit_decay_rate(ts[2:], amps[2:]) / (k2 * nu)
+    assert rates["LOCAL"] == pytest.approx(1.0, abs=0.015)
+    assert abs(rates["NONE"] - 1.0) > 0.5
+
+
+def test_taylor_green_3d_decay_and_conservation(oracle_mod):
+    """3-D Taylor-Green on the 32x32x16 lattice with r = 1, s = 0.5, nu = 0.01: the
+    projection on the initial mode decays as exp(-nu |k|^2 t) (linear regime, small
+    u0); the uncorrected scheme does not.  Mass is conserved to round-off and the
+    total momentum stays zero."""
+    n, r, s, cs2, nu = (32, 32, 16), 1.0, 0.5, 1 / 12, 0.01
+    rho, u, k = synth.taylor_green_3d(*n, r, s, 0.002)
+    res = {}
+    for corr in ("LOCAL", "NONE"):
+        o = _make(oracle_mod, n, r, s, cs2, nu, corr)
+        f0 = o.init(rho, u)
+        ts, amps = _decay(o, rho, u, 100, 10)
+        res[corr] = fit_decay_rate(ts[1:], amps[1:]) / (k @ k * nu)
+    assert res["LOCAL"] == pytest.approx(1.0, abs=0.04)
+    assert abs(res["NONE"] - 1.0) > 0.2
+    o = _make(oracle_mod, n, r, s, cs2, nu, "LOCAL")
+    f = o.run(f0, 20)
+    assert f.sum() == pytest.approx(f0.sum(), rel=1e-14)
+    ec = o.velocities() * np.array([[1.0], [r], [s]])
+    np.testing.assert_allclose(np.einsum("iq,qzyx->i", ec, f), 0.0, atol=1e-10)
+
+
+def test_uniform_force_adds_momentum(oracle_mod):
+    """Periodic lattice: every step adds N F to the total momentum sum_x sum_a f e."""
+    n, r, s = (4, 6, 5), 0.5, 2.0
+    F = np.array([1e-5, -2e-5, 3e-5])
+    o = _make(oracle_mod, n, r, s, 1 / 12, 0.03, force=tuple(F))
+    rho, u = synth.solenoidal_random(*n, r, s, 2.0, 0.01, seed=1)
+    f0 = o.init(rho, u)
+    f = o.run(f0, 7)
+    ec = o.velocities() * np.array([[1.0], [r], [s]])
+    p0, p1 = np.einsum("iq,qzyx->i", ec, f0), np.einsum("iq,qzyx->i", ec, f)
+    np.testing.assert_allclose(p1 - p0, 7 * np.prod(n) * F, rtol=1e-10, atol=1e-15)
+
+
+@pytest.mark.parametrize("r,s,cs2,nu,ny,nz", [(0.5, 1.0, 0.04, 0.02, 20, 10), (1.0, 0.5, 0.10, 0.01, 10, 20)])
+def test_duct_matches_series(oracle_mod, r, s, cs2, nu, ny, nz):
+    """Body-force driven flow in a duct with half-way bounce-back walls on y and z
+    (walls half a spacing beyond the outer nodes) converges to the series solution
+    (Eq. 70 generalised to a rectangle); parameters as in Table 1 rows 3 and 1 on a
+    coarser square cross-section of side 10.  Mass is conserved exactly."""
+    Fx = 1e-5
+    o = _make(oracle_mod, (1, ny, nz), r, s, cs2, nu, walls="yz", force=(Fx, 0.0, 0.0))
+    f0 = o.init(np.ones((nz, ny, 1)), np.zeros((3, nz, ny, 1)))
+    f = o.run(f0, 4000)
+    assert f.sum() == pytest.approx(f0.sum(), rel=1e-13)
+    _, u = o.moments(f)
+    a, b = ny * r / 2, nz * s / 2
+    Z, Y = np.meshgrid((np.arange(nz) + 0.5) * s - b, (np.arange(ny) + 0.5) * r - a, indexing="ij")
+    ua = duct_series(Y, Z, a, b, Fx, 1.0, nu)
+    ux = u[0][:, :, 0]
+    assert np.linalg.norm(ux - ua) / np.linalg.norm(ua) < 0.02
+    assert np.abs(u[1:]).max() < 1e-6 * np.abs(ux).max()   # no secondary flow
+
+
+def test_duct_series_solves_poisson_problem():
+    """The series satisfies nu (u_yy + u_zz) = -F/rho inside and vanishes on the walls."""
+    a, b, F, nu = 5.0, 3.0, 1e-5, 0.02
+    h = 1e-3
+    for (y, z) in [(0.3, -1.1), (-2.0, 2.0), (4.0, 0.5)]:
+        lap = (duct_series(y + h, z, a, b, F, 1, nu) + duct_series(y - h, z, a, b, F, 1, nu)
+               + duct_series(y, z + h, a, b, F, 1, nu) + duct_series(y, z - h, a, b, F, 1, nu)
+               - 4 * duct_series(y, z, a, b, F, 1, nu)) / h ** 2
+        assert nu * lap == pytest.approx(-F, rel=5e-3)   # Fourier series of a constant: slow convergence
+    for (y, z) in [(a, 1.0), (-a, -2.0), (0.7, b), (-1.0, -b)]:
+        assert abs(duct_series(y, z, a, b, F, 1, nu)) < 1e-6 * duct_series(0, 0, a, b, F, 1, nu)
+
+
+def test_moving_lid_terms_match_eq69(oracle_mod):
+    """The generic momentum-augmented bounce-back (Eq. momentumaugmentedBBscheme with
+    f^eq = Q^-1 m^eq) reproduces the printed cuboid-lattice terms of Eq. 69."""
+    r, s, cs2, rho, U = 0.5, 0.8, 0.04, 1.03, 0.07
+    o = oracle_mod.Oracle(r=r, s=s, cs2=cs2)
+    feq = o.equilibrium(rho, [U, 0.0, 0.0])
+    for inc, (out, c) in lid_bounce_coefficients_eq69(r, s, cs2).items():
+        assert -(feq[out] - feq[inc]) == pytest.approx(c * rho * U, abs=1e-15), inc
+
+
+def test_couette_flow_is_linear(oracle_mod):
+    """Plane Couette flow between a wall at rest and a lid moving along x: the steady
+    profile is the exact linear one at the half-way wall positions."""
+    r, s, cs2, nu, ny, U = 0.5, 1.0, 0.04, 0.02, 10, 0.01
+    o = _make(oracle_mod, (1, ny, 1), r, s, cs2, nu, walls="y", lid_u=U)
+    f = o.run(o.init(np.ones((1, ny, 1)), np.zeros((3, 1, ny, 1))), 3000)
+    _, u = o.moments(f)
+    y = (np.arange(ny) + 0.5) * r
+    np.testing.assert_allclose(u[0][0, :, 0], U * y / (ny * r), atol=1e-8 * U)
+
+
+def test_local_strain_rates_match_velocity_gradients(oracle_mod):
+    """Eq. 44-49 recover the diagonal velocity gradients from the non-equilibrium
+    moments: compared with the spectral derivative of the simulated velocity field
+    of a decaying Taylor-Green vortex in the (x, z) plane of an r=1, s=0.5 lattice."""
+    r, s, cs2, nu, n = 1.0, 0.5, 1 / 12, 0.02, (16, 1, 32)
+    o = _make(oracle_mod, n, r, s, cs2, nu)
+    rho, u, _ = synth.taylor_green_2d(*n, r, s, 1e-3, "xz")
+    f = o.run(o.init(rho, u), 60)
+    rr, uu = o.moments(f)
+    kx = 2 * np.pi * np.fft.fftfreq(n[0], d=1.0)
+    kz = 2 * np.pi * np.fft.fftfreq(n[2], d=s)
+    dxux = np.real(np.fft.ifft(1j * kx * np.fft.fft(uu[0], axis=2), axis=2))
+    dzuz = np.real(np.fft.ifft(1j * kz[:, None, None] * np.fft.fft(uu[2], axis=0), axis=0))
+    rec = np.zeros((3,) + uu.shape[1:])
+    for z in range(n[2]):
+        for x in range(n[0]):
+            un = uu[:, z, 0, x]
+            rec[:, z, 0, x] = o.strain_rates(o.M(un) @ f[:, z, 0, x], rr[z, 0, x], un)
+    scale = np.abs(dxux).max()
+    assert np.abs(rec[0] - dxux).max() < 0.03 * scale
+    assert np.abs(rec[2] - dzuz).max() < 0.03 * scale
+    assert np.abs(rec[1]).max() < 0.01 * scale
