@@ -1,0 +1,346 @@
+"""Benchmark of the fused collide-and-stream step (MLUPS and fraction of the HBM roofline).
+
+Default workload: the large periodic anisotropic decaying flow, 512 x 256 x 256 nodes,
+r_y = r_z = 0.5, cs2 = 1/12, nu = 0.005, omega_xi = 1, seeded random solenoidal
+velocity (Gaussian spectrum peak k = 4, u_rms = 0.03), FP32 arithmetic; populations
+stored as FP32 (the headline value) and as shifted FP32 / BF16 / FP16 (reported
+beside it with their velocity error against the FP64 path).
+
+One step = one fused launch over the whole lattice.  The working set (2 x 27 x N
+stored values, >= 3.6 GB) is far larger than L2, so no explicit flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent replica of
+the workload on its own GPU ("replicas only": the update has no collective);
+value = total node updates of all ranks / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline, plain FP32 vs reduced-precision storage at stated error"
+WORKLOAD = dict(workload="decaying anisotropic flow 512x256x256, r_y=0.5, r_z=0.5 (periodic)",
+                nx=512, ny=256, nz=256, r_y=0.5, r_z=0.5, cs2=1.0 / 12.0, nu=0.005, omega_xi=1.0,
+                init="seeded solenoidal velocity, spectrum peak k=4, u_rms=0.03, seed 3", corr="local")
+BYTES_PER_NODE = {"f64": 432, "f32": 216, "f32s": 216, "f16s": 108, "bf16s": 108}
+VARIANTS = ["f32", "f32s", "bf16s", "f16s"]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    w = WORKLOAD
+    rho, u = synth.solenoidal_random(w["nx"], w["ny"], w["nz"], w["r_y"], w["r_z"], 4.0, 0.03, seed=3)
+    return rho, u
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2107_14774_gb300 import Lattice
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    dims = (w["nx"], w["ny"], w["nz"])
+    N = w["nx"] * w["ny"] * w["nz"]
+    rho, u = make_inputs()
+    rho_t = torch.from_numpy(rho.astype(np.float32)).to(dev)
+    u_t = torch.from_numpy(u.astype(np.float32)).to(dev)
+    stream = torch.cuda.Stream(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    variants = args.variants.split(",")
+    results = {}
+    kernel_ms = {}
+    for var in variants:
+        lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var,
+                      corr=w["corr"], stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            lat.init(rho_t, u_t)
+            lat.step(args.warmup)
+        stream.synchronize()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with ClockSampler(dev.index) as clk:
+            ev0.record(stream)
+            lat.step(args.steps)
+            ev1.record(stream)
+            ev1.synchronize()
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kernel_ms[var] = ms / args.steps
+        results[var] = {"mlups": N * args.steps * world / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+                        "clocks": clk.summary()}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    barrier()
+
+    # velocity error of each storage form against the FP64 path after the same steps
+    err_steps = args.error_steps
+    if err_steps <= 0:
+        for var in variants:
+            results[var]["u_rel_err_vs_f64"] = None
+        return results, kernel_ms, run_e2e(args, rho, u, dims, stream, dev, world, barrier), N
+    ref = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage="f64", corr=w["corr"],
+                  stream=stream, device=dev)
+    with torch.cuda.stream(stream):
+        ref.init(rho_t.double(), u_t.double()).step(err_steps)
+    _, u_ref = ref.moments()
+    ref.close()
+    del ref
+    torch.cuda.empty_cache()
+    for var in variants:
+        lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var, corr=w["corr"],
+                      stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            lat.init(rho_t, u_t).step(err_steps)
+        _, uu = lat.moments()
+        results[var]["u_rel_err_vs_f64"] = float(torch.linalg.vector_norm(uu.double() - u_ref)
+                                                 / torch.linalg.vector_norm(u_ref))
+        lat.close()
+        del lat
+    del u_ref
+    torch.cuda.empty_cache()
+    return results, kernel_ms, run_e2e(args, rho, u, dims, stream, dev, world, barrier), N
+
+
+def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
+    """End-to-end MLUPS through the public API with pinned host buffers."""
+    import torch
+
+    from paper_2107_14774_gb300 import Lattice
+    if args.no_e2e:
+        return None
+    w = WORKLOAD
+    N = dims[0] * dims[1] * dims[2]
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    # end to end through the public API with pinned host buffers: every step copies
+    # the inputs (rho, u) host->device (lb_init), runs one fused step and reads the
+    # resulting fields device->host (lb_moments)
+    rho_h = torch.from_numpy(rho.astype(np.float32)).pin_memory()
+    u_h = torch.from_numpy(u.astype(np.float32)).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage="f32", corr=w["corr"],
+                  stream=stream, device=dev)
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        lat.init(rho_h, u_h).step(1).moments(rho_o, u_o)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.init(rho_h, u_h).step(1).moments(rho_o, u_o)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    lat.close()
+    e2e = {"value": N * e2e_steps * world / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 16 * N,
+           "d2h_bytes_per_step": 16 * N,
+           "what": "lb_init from pinned host rho,u + lb_step(1) + lb_moments to pinned host, per step"}
+    return e2e
+
+
+def oracle_sample(seconds_target=15.0, cores=None):
+    """The FP64 oracle as it stands, on the host cores, on a z-slab of the workload."""
+    import oracle
+    oracle.build()
+    w = WORKLOAD
+    rho, u = make_inputs()
+    wn = 1.0 / (w["nu"] / w["cs2"] + 0.5)
+    nzs = 8
+    o = oracle.Oracle(w["nx"], w["ny"], nzs, r=w["r_y"], s=w["r_z"], cs2=w["cs2"], omega_nu=wn, omega_xi=1.0,
+                      corr=oracle.CORR_LOCAL, threads=cores or 0)
+    f = o.init(rho[:nzs], u[:, :nzs])
+    n = w["nx"] * w["ny"] * nzs
+    t0 = time.perf_counter()
+    f = o.step(f)
+    dt = time.perf_counter() - t0
+    steps = 1
+    # grow the sample to roughly the target duration
+    extra = int(max(0, seconds_target / max(dt, 1e-3) - 1))
+    extra = min(extra, 20)
+    if extra:
+        t0 = time.perf_counter()
+        f = o.run(f, extra)
+        dt += time.perf_counter() - t0
+        steps += extra
+    return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": o.threads, "kind": "oracle",
+            "sample": f"{steps} steps of a {w['nx']}x{w['ny']}x{nzs} periodic z-slab of the workload "
+                      f"(FP64 C oracle, factored form, OpenMP), {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--error-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variants", default=",".join(VARIANTS),
+                    help="storage forms to time (comma list of f32,f32s,bf16s,f16s,f64)")
+    ap.add_argument("--dims", default=None,
+                    help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.dims:
+        nx, ny, nz = (int(v) for v in args.dims.split(","))
+        WORKLOAD.update(nx=nx, ny=ny, nz=nz,
+                        workload=f"decaying anisotropic flow {nx}x{ny}x{nz}, r_y=0.5, r_z=0.5 (periodic)")
+    config = {k: WORKLOAD[k] for k in ("workload", "r_y", "r_z", "cs2", "nu", "omega_xi", "init", "corr")}
+    config.update(nodes=WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"], parallelism=f"replicas x{world}",
+                  l2="working set (2 x 27 x N stored values) >> 129 MB L2; no flush needed")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cpu = oracle_sample(seconds_target=max(5.0, 2.0 * args.steps))
+        line = {"impl": "reference", "metric": METRIC, "value": cpu["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": cpu,
+                "e2e": {"value": cpu["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    results, kernel_ms, e2e, N = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, which = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    main_var = "f32" if "f32" in results else list(results)[0]
+    r = results[main_var]
+    achieved = BYTES_PER_NODE[main_var] * N / (kernel_ms[main_var] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": f"{which} hbm_gbs (copy bandwidth)", "kernel": f"k_step<{main_var}, LB_CORR_LOCAL>",
+            "algorithmic_bytes_per_launch": BYTES_PER_NODE[main_var] * N}
+    variants = {}
+    for var in results:
+        v = results[var]
+        ach = BYTES_PER_NODE[var] * N / (kernel_ms[var] * 1e-3) / 1e9
+        variants[var] = {"mlups": round(v["mlups"], 1), "ms_per_step": round(v["ms_per_step"], 4),
+                         "bytes_per_node": BYTES_PER_NODE[var], "achieved_gbs": round(ach, 1),
+                         "hbm_frac": round(ach / peak, 4),
+                         f"u_rel_err_vs_f64_after_{args.error_steps}_steps": v["u_rel_err_vs_f64"],
+                         "clocks": v["clocks"]}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = oracle_sample()
+    line = {"metric": METRIC, "value": round(r["mlups"], 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_var == "f64" else "f32", "data": "synthetic", "config": config,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "storage": main_var,
+            "clocks": r["clocks"], "variants": variants}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * lbcuboid.h -- C ABI of the GB300 (sm_103a) implementation of the fused
+ * collide-and-stream update of the cuboid-lattice D3Q27 central-moment lattice
+ * Boltzmann method (3DCCM-LBM) of Yahia, Schupbach & Premnath,
+ * arXiv:2107.14774.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice units (Sec. 2.1): dx = dt = 1, dy = r_y, dz = r_z.  The 27 particle
+ * velocities are e_a = (ex, r_y ey, r_z ez) with (ex, ey, ez) the integer D3Q27
+ * stencil in the paper's ordering (Eq. 1a-1c).
+ * Node (i, j, k), 0 <= i < nx, ... is stored at index n = i + nx (j + ny k);
+ * N = nx ny nz.  Populations are [27][N] (direction-major), density [N],
+ * velocity and force [3][N].
+ * "real" below is double when the context stores LB_F64 populations and float
+ * otherwise (see lb_real_size).
+ * A pointer argument may point to device memory or to host memory (pageable or
+ * pinned): the library inspects it (cudaPointerGetAttributes) and copies
+ * through the context's stream when it is a host pointer.  Caller pointers are
+ * only borrowed for the duration of the call; the library copies what it keeps.
+ * All work is issued on the context's CUDA stream.  Calls that return host
+ * data synchronise that stream.
+ *
+ * Errors: every call returns an lb_status; nothing aborts or throws.  Parameter
+ * errors are reported synchronously (LB_EINVAL); asynchronous CUDA errors
+ * surface as LB_ECUDA at the next call that synchronises.  lb_last_error()
+ * returns a thread-local message for the last failure.
+ *
+ * Ownership: the context owns its two population buffers and scratch memory
+ * (cudaMalloc at creation, cudaFree at lb_destroy).
+ */
+#ifndef LBCUBOID_H
+#define LBCUBOID_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,     /* bad argument (sizes, rates, pointer, state) */
+    LB_ENOMEM = 2,     /* device allocation failed */
+    LB_ECUDA = 3,      /* CUDA runtime error (message in lb_last_error) */
+    LB_EUNSTABLE = 4,  /* non-finite or non-positive density found */
+    LB_ETIMEOUT = 5,   /* a bounded wait ran out */
+    LB_ESTATE = 6      /* call not valid in the context's current state */
+} lb_status;
+
+/* Population storage.  Arithmetic is FP64 for LB_F64 and FP32 for the others.
+ * The shifted forms store g_a = f_a - w_a rho0 (rho0 = 1, w_a the rest weights
+ * f^eq_a(1, 0)); LB_F16_SHIFTED scales each direction by an exact power of two
+ * before rounding to binary16 (round to nearest even), LB_BF16_SHIFTED rounds to
+ * bfloat16 (round to nearest even). */
+typedef enum {
+    LB_F64 = 0,
+    LB_F32 = 1,
+    LB_F32_SHIFTED = 2,
+    LB_F16_SHIFTED = 3,
+    LB_BF16_SHIFTED = 4
+} lb_storage;
+
+/* Second-order equilibrium corrections (Eq. 29-30, 38-40; App. D).
+ * NONE: uncorrected cuboid scheme.  LOWMACH: anisotropy terms only (the
+ * low-Mach coefficients of Sec. 2.5; no 3u^2 terms, no density gradients).
+ * LOCAL: full theta coefficients from the locally recovered diagonal strain
+ * rates (Eq. 44-49) with the density-gradient terms dropped.  FULL: LOCAL plus
+ * the lambda and e-terms with grad(rho) from second-order central differences
+ * of the current density (one-sided next to walls). */
+typedef enum {
+    LB_CORR_NONE = 0,
+    LB_CORR_LOWMACH = 1,
+    LB_CORR_LOCAL = 2,
+    LB_CORR_FULL = 3
+} lb_corr;
+
+#define LB_WALL_X 1u   /* walls normal to x at i = -1/2 and i = nx - 1/2 */
+#define LB_WALL_Y 2u
+#define LB_WALL_Z 4u
+
+typedef struct {
+    int nx, ny, nz;        /* >= 1 each */
+    double r_y, r_z;       /* grid aspect ratios r = dy/dx, s = dz/dx (> 0) */
+    double nu;             /* shear viscosity > 0: omega_nu = 1/(nu/cs2 + 1/2) (Eq. 53) */
+    double zeta;           /* bulk viscosity > 0: omega_xi = 1/(3 zeta/(2 cs2) + 1/2) (Eq. 53);
+                              zeta <= 0 selects omega_xi = 1 */
+    double cs2;            /* squared sound speed; 0 selects min(1, r^2, s^2)/3 (Sec. 2.5);
+                              must satisfy 0 < cs2 < min(1, r^2, s^2) */
+    int storage;           /* lb_storage */
+    int corr;              /* lb_corr */
+    unsigned wall_mask;    /* LB_WALL_* bits: half-way bounce-back walls (Sec. 4); other axes periodic */
+    double force[3];       /* uniform body force (lattice units), Eq. 11c */
+    double lid_u;          /* velocity along x of the wall at j = ny - 1/2 (needs LB_WALL_Y);
+                              momentum-augmented bounce-back (Sec. 4, Eq. 69); 0 = at rest */
+    void *stream;          /* cudaStream_t to issue all work on; NULL = the legacy default stream */
+} lb_config;
+
+/* Fill *cfg with defaults: FP32 storage, LOCAL corrections, periodic, no
+ * force, omega_xi = 1, cs2 = min(1, r^2, s^2)/3. */
+void lb_config_default(lb_config *cfg, int nx, int ny, int nz, double r_y, double r_z, double nu);
+
+/* Create a context with the defaults above (lb_create(nx,ny,nz,r_y,r_z,nu,zeta)).
+ * zeta <= 0 selects omega_xi = 1.  *out receives the context. */
+lb_status lb_create(int nx, int ny, int nz, double r_y, double r_z, double nu, double zeta,
+                    lb_ctx **out);
+
+/* Create a context from a full configuration. */
+lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out);
+
+/* Release every resource of the context (synchronises its stream).  NULL is ignored. */
+void lb_destroy(lb_ctx *ctx);
+
+/* Bytes of one "real" of this context: 8 (LB_F64) or 4. */
+int lb_real_size(const lb_ctx *ctx);
+
+/* Nodes N = nx ny nz. */
+size_t lb_num_nodes(const lb_ctx *ctx);
+
+/* Relaxation rates and sound speed in use: out[0] = omega_nu, out[1] = omega_xi, out[2] = cs2. */
+lb_status lb_get_params(const lb_ctx *ctx, double out[3]);
+
+/* Initialise the populations to the equilibrium f^eq(rho, u) (Eq. 9, 10) at every
+ * node; rho [N] and u [3][N] in the context's real type.  The density and
+ * velocity returned by lb_moments right after lb_init are rho and u + F/(2 rho). */
+lb_status lb_init(lb_ctx *ctx, const void *rho, const void *u);
+
+/* Optional per-node body force [3][N] (real), added to the uniform force; copied
+ * into the context.  NULL removes it. */
+lb_status lb_set_force_field(lb_ctx *ctx, const void *force);
+
+/* Enqueue n fused collide-and-stream steps (Sec. 3.2 algorithm; Apps. A-G) on the
+ * context's stream.  Asynchronous; errors of the launches are reported here,
+ * errors during execution at the next synchronising call. */
+lb_status lb_step(lb_ctx *ctx, int n);
+
+/* Density [N] and velocity [3][N] (real) of the current populations:
+ * rho = sum f, rho u = sum f e + F/2 (Eq. 12).  Synchronises. */
+lb_status lb_moments(lb_ctx *ctx, void *rho, void *u);
+
+/* FP64 global sums out[0] = sum rho, out[1..3] = sum rho u (host array), computed
+ * with a deterministic two-pass reduction.  Returns LB_EUNSTABLE (with the sums
+ * still written) if any node has a non-finite or non-positive density or a
+ * non-finite velocity.  Synchronises. */
+lb_status lb_reduce(lb_ctx *ctx, double out_mass_momentum[4]);
+
+/* Copy the pre-collision populations f_a(x, t) [27][N] (real) out of / into the
+ * context.  Exact for LB_F64 and LB_F32; the shifted forms convert between f and
+ * the stored g = f - w rho0 in the real type. */
+lb_status lb_get_populations(lb_ctx *ctx, void *dst);
+lb_status lb_set_populations(lb_ctx *ctx, const void *src);
+
+/* Raw checkpoint of the stored state: lb_state_bytes() bytes in the library's
+ * internal layout (27 N stored values), copied out of / into the context.
+ * Resuming from it is bit-identical to an uninterrupted run. */
+size_t lb_state_bytes(const lb_ctx *ctx);
+lb_status lb_get_state(lb_ctx *ctx, void *dst);
+lb_status lb_set_state(lb_ctx *ctx, const void *src, long long time_step);
+
+/* Number of completed time steps since the last lb_init / lb_set_populations. */
+long long lb_time_step(const lb_ctx *ctx);
+
+/* Message of the last error on this thread ("" if none). */
+const char *lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBCUBOID_H */

@@ -1,0 +1,289 @@
+// collide.cuh -- per-node collision of the cuboid D3Q27 central-moment scheme
+// (Sec. 3.2; Apps. A-G), written for registers and for the deviation form.
+//
+// The node state enters and leaves as deviations h_a = f_a - w_a from the rest
+// weights (rho0 = 1).  The transforms P, S, F(u) and their inverses are applied
+// in their separable one-dimensional form: the monomial basis {1, e, e^2} per
+// axis and the three velocities {-c, 0, c} per axis make P, S and F(u) tensor
+// products of 3x3 factors, so the 27x27 products of Apps. A-C and E-G reduce to
+// nine 3-point transforms per axis.  Because every relaxation rate other than
+// omega_nu and omega_xi is 1 (App. D), the post-collision central moments equal
+// their Maxwellian equilibria (Eq. 9) except
+//   k~_100 = F_x / 2 (and y, z),  k~_110 = (1 - omega_nu) k_110 (and 101, 011),
+//   the three diagonal second-order moments (relaxed via B, B^-1 with the
+//   corrected equilibria of Eq. 63 / App. D);
+// so only the ten raw moments of order <= 2 are needed on the way in, and on the
+// way out f~ = f^eq(rho, u) + M(u)^-1 (k~ - k^eq), where the second term has only
+// nine non-zero central-moment inputs.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace lbc {
+
+// Per-axis columns of the inverse central-moment transform M(u)^-1 for one axis
+// with speed c and velocity u (velocity index v = -1, 0, +1 -> [0], [1], [2]):
+// the 1-D populations whose central moments about u are (1,0,0), (0,1,0),
+// (0,0,1).  Raw moments (1, u, u^2), (0, 1, 2u), (0, 0, 1) mapped to the three
+// velocities by g(0) = M0 - M2/c^2, g(+-c) = (M2/c^2 +- M1/c)/2.
+template <class T>
+struct AxisCols {
+    T g0[3], g1[3], g2[3];  // columns for central moments of order 0, 1, 2
+    T phi[3], dphi[3];      // equilibrium factor phi = g0 + cs2 g2 and phi - w
+    T w[3];                 // 1-D rest weights
+};
+
+template <class T>
+__device__ __forceinline__ AxisCols<T> axis_cols(T u, T ic, T ic2, T w0, T wpm, T cs2)
+{
+    AxisCols<T> A;
+    const T a = u * ic;        // u / c
+    const T b = a * a;         // u^2 / c^2
+    const T hb = T(0.5) * b, ha = T(0.5) * a;
+    A.g0[0] = hb - ha;
+    A.g0[1] = T(1) - b;
+    A.g0[2] = hb + ha;
+    const T hic = T(0.5) * ic;
+    const T aic = a * ic;      // u / c^2
+    A.g1[0] = aic - hic;
+    A.g1[1] = T(-2) * aic;
+    A.g1[2] = aic + hic;
+    A.g2[0] = T(0.5) * ic2;
+    A.g2[1] = -ic2;
+    A.g2[2] = T(0.5) * ic2;
+    A.dphi[0] = A.g0[0];
+    A.dphi[1] = -b;
+    A.dphi[2] = A.g0[2];
+    A.w[0] = wpm;
+    A.w[1] = w0;
+    A.w[2] = wpm;
+    A.phi[0] = wpm + A.dphi[0];
+    A.phi[1] = w0 + A.dphi[1];
+    A.phi[2] = wpm + A.dphi[2];
+    (void)cs2;
+    return A;
+}
+
+// Hydrodynamic output of a collision.
+template <class T>
+struct NodeMacro {
+    T rho, ux, uy, uz;
+};
+
+// Pre-collision moments of order <= 2 of one node, from the deviations h.
+// Cubic raw moments are summed along x-lines, then y, then z (App. A in
+// separable form); the cuboid scaling S (Eq. 59, App. B) follows.
+template <class T>
+struct RawMoments {
+    T dr;                      // sum h   (rho - 1)
+    T jx, jy, jz;              // sum h e (cuboid e)
+    T pxx, pyy, pzz, pxy, pxz, pyz;  // sum h e_i e_j
+};
+
+template <class T>
+__device__ __forceinline__ RawMoments<T> raw_moments(const T (&h)[Q], const Phys<T> &P)
+{
+    // x-lines: for each (ey, ez) the sums over ex of h, h ex, h ex^2
+    T X0[3][3], X1[3][3], X2[3][3];
+#pragma unroll
+    for (int jy = 0; jy < 3; ++jy)
+#pragma unroll
+        for (int jz = 0; jz < 3; ++jz) {
+            const T hm = h[dir_of(-1, jy - 1, jz - 1)];
+            const T h0 = h[dir_of(0, jy - 1, jz - 1)];
+            const T hp = h[dir_of(1, jy - 1, jz - 1)];
+            const T t = hp + hm;
+            X0[jy][jz] = t + h0;
+            X1[jy][jz] = hp - hm;
+            X2[jy][jz] = t;
+        }
+    // y stage (only the combinations of total order <= 2 are kept)
+    T Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
+#pragma unroll
+    for (int jz = 0; jz < 3; ++jz) {
+        const T s = X0[2][jz] + X0[0][jz];
+        Y00[jz] = s + X0[1][jz];
+        Y01[jz] = X0[2][jz] - X0[0][jz];
+        Y02[jz] = s;
+        Y10[jz] = X1[0][jz] + X1[1][jz] + X1[2][jz];
+        Y11[jz] = X1[2][jz] - X1[0][jz];
+        Y20[jz] = X2[0][jz] + X2[1][jz] + X2[2][jz];
+    }
+    RawMoments<T> m;
+    const T s00 = Y00[2] + Y00[0];
+    m.dr = s00 + Y00[1];
+    const T m001 = Y00[2] - Y00[0];
+    const T m002 = s00;
+    const T m010 = Y01[0] + Y01[1] + Y01[2];
+    const T m011 = Y01[2] - Y01[0];
+    const T m020 = Y02[0] + Y02[1] + Y02[2];
+    const T m100 = Y10[0] + Y10[1] + Y10[2];
+    const T m101 = Y10[2] - Y10[0];
+    const T m110 = Y11[0] + Y11[1] + Y11[2];
+    const T m200 = Y20[0] + Y20[1] + Y20[2];
+    // S: scale by r^n s^p (Eq. 59)
+    const T r = P.c[1], s = P.c[2];
+    m.jx = m100;
+    m.jy = r * m010;
+    m.jz = s * m001;
+    m.pxx = m200;
+    m.pyy = (r * r) * m020;
+    m.pzz = (s * s) * m002;
+    m.pxy = r * m110;
+    m.pxz = s * m101;
+    m.pyz = (r * s) * m011;
+    return m;
+}
+
+// One collision, in place on the deviations h (Sec. 3.2 steps, App. D).
+// F: body force at the node; gr: density gradient (used by LB_CORR_FULL only).
+template <class T, int CORR>
+__device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T Fx, T Fy, T Fz,
+                                                T grx = T(0), T gry = T(0), T grz = T(0))
+{
+    const RawMoments<T> m = raw_moments(h, P);
+    const T cs2 = P.cs2;
+    const T dr = m.dr;
+    const T rho = T(1) + dr;
+    const T irho = T(1) / rho;
+    // rho u = sum f e + F/2 (Eq. 12)
+    const T ux = (m.jx + T(0.5) * Fx) * irho;
+    const T uy = (m.jy + T(0.5) * Fy) * irho;
+    const T uz = (m.jz + T(0.5) * Fz) * irho;
+
+    // second-order central moments (App. C), diagonal ones as deviations from cs2 rho:
+    // k_200 - cs2 rho = sum h ex^2 - cs2 (rho - 1) - rho ux^2 + ux Fx, etc.
+    const T n200 = m.pxx - cs2 * dr - rho * ux * ux + ux * Fx;
+    const T n020 = m.pyy - cs2 * dr - rho * uy * uy + uy * Fy;
+    const T n002 = m.pzz - cs2 * dr - rho * uz * uz + uz * Fz;
+    const T k110 = m.pxy - rho * ux * uy + T(0.5) * (ux * Fy + uy * Fx);
+    const T k101 = m.pxz - rho * ux * uz + T(0.5) * (ux * Fz + uz * Fx);
+    const T k011 = m.pyz - rho * uy * uz + T(0.5) * (uy * Fz + uz * Fy);
+
+    // B: combined diagonal moments (App. D); N2s = k_2s - 3 cs2 rho
+    const T N2s = n200 + n020 + n002;
+    const T k2d1 = n200 - n020;
+    const T k2d2 = n200 - n002;
+
+    // corrected equilibria of the combined moments (App. D, Eq. 63), as deviations
+    T E2s = T(0), E2d1 = T(0), E2d2 = T(0);
+    if (CORR != LB_CORR_NONE) {
+        const T al = (CORR == LB_CORR_LOWMACH) ? T(0) : T(1);
+        const T ux2 = al * ux * ux, uy2 = al * uy * uy, uz2 = al * uz * uz;
+        // density-gradient terms (FULL only): A, B, C and e-terms
+        T ebr = T(0), esr1 = T(0), esr2 = T(0);
+        if (CORR == LB_CORR_FULL) {
+            const T A = T(0.5) * P.an[0] * ux, B = T(0.5) * P.an[1] * uy, C = T(0.5) * P.an[2] * uz;
+            esr1 = -A * grx + B * gry;
+            esr2 = -A * grx + C * grz;
+            ebr = -A * grx - B * gry - C * grz;
+        }
+        const T Rb = N2s + ebr, Rs1 = k2d1 + esr1, Rs2 = k2d2 + esr2;
+        const T hx = T(0.5) * P.an[0] + T(1.5) * ux2;
+        const T hy = T(0.5) * P.an[1] + T(1.5) * uy2;
+        const T hz = T(0.5) * P.an[2] + T(1.5) * uz2;
+        const T Csx = (hx - P.two_cs2_wn) * rho;
+        const T Cbx = (hx - P.two_cs2_wb) * rho;
+        const T Csy = (P.two_cs2_wn - hy) * rho;
+        const T Cby = (hy - P.two_cs2_wb) * rho;
+        const T Csz = (P.two_cs2_wn - hz) * rho;
+        const T Cbz = (hz - P.two_cs2_wb) * rho;
+        // Eq. 49 / App. D: Cramer's rule on the 3x3 system
+        const T num = -Csz * Cby * Rs1 - Csy * (Cbz * Rs2 - Csz * Rb);
+        const T den = -Csx * Csz * Cby - Csy * (Csx * Cbz - Csz * Cbx);
+        const T dxux = num / den;
+        const T dyuy = (Rs1 - Csx * dxux) / Csy;
+        const T dzuz = (Rs2 - Csx * dxux) / Csz;
+        // theta coefficients (Eq. 38-40 in the shear/bulk notation of App. D)
+        const T qx = -rho * (T(3) * ux2 + P.an[0]);
+        const T qy = -rho * (T(3) * uy2 + P.an[1]);
+        const T qz = -rho * (T(3) * uz2 + P.an[2]);
+        E2s = P.tb * (qx * dxux + qy * dyuy + qz * dzuz);
+        E2d1 = P.tn * (qx * dxux - qy * dyuy);
+        E2d2 = P.tn * (qx * dxux - qz * dzuz);
+        if (CORR == LB_CORR_FULL) {
+            // lambda coefficients: s-terms -, +, + ; b-terms -, -, -
+            const T lx = P.an[0] * ux, ly = P.an[1] * uy, lz = P.an[2] * uz;
+            E2s -= P.tb * (lx * grx + ly * gry + lz * grz);
+            E2d1 += P.tn * (-lx * grx + ly * gry);
+            E2d2 += P.tn * (-lx * grx + lz * grz);
+        }
+    }
+    // relaxation (App. D)
+    const T wn = P.wn, wb = P.wb;
+    const T t2s = N2s + wb * (E2s - N2s);
+    const T t2d1 = k2d1 + wn * (E2d1 - k2d1);
+    const T t2d2 = k2d2 + wn * (E2d2 - k2d2);
+    const T onemw = T(1) - wn;
+    const T t110 = onemw * k110, t101 = onemw * k101, t011 = onemw * k011;
+    // B^-1 (end of App. D), deviations of k~_200, k~_020, k~_002 from cs2 rho
+    const T third = T(1) / T(3);
+    const T d200 = (t2s + t2d1 + t2d2) * third;
+    const T d020 = (t2s - T(2) * t2d1 + t2d2) * third;
+    const T d002 = (t2s + t2d1 - T(2) * t2d2) * third;
+    const T hFx = T(0.5) * Fx, hFy = T(0.5) * Fy, hFz = T(0.5) * Fz;
+
+    // back to populations: f~ = f^eq(rho,u) + M(u)^-1 (k~ - k^eq)  (Apps. E-G)
+    const AxisCols<T> X = axis_cols(ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0], cs2);
+    const AxisCols<T> Y = axis_cols(uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1], cs2);
+    const AxisCols<T> Z = axis_cols(uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2], cs2);
+
+    // z stage of M^-1 on the sparse non-equilibrium central moments
+    T A00[3], A10[3], A01[3], A11[3], A20[3], A02[3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+        A00[z] = hFz * Z.g1[z] + d002 * Z.g2[z];
+        A10[z] = hFx * Z.g0[z] + t101 * Z.g1[z];
+        A01[z] = hFy * Z.g0[z] + t011 * Z.g1[z];
+        A11[z] = t110 * Z.g0[z];
+        A20[z] = d200 * Z.g0[z];
+        A02[z] = d020 * Z.g0[z];
+    }
+    // equilibrium factors: P_yz = phi_y phi_z, D_yz = phi_y phi_z - w_y w_z
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+            const T B0 = A00[z] * Y.g0[y] + A01[z] * Y.g1[y] + A02[z] * Y.g2[y];
+            const T B1 = A10[z] * Y.g0[y] + A11[z] * Y.g1[y];
+            const T B2 = A20[z] * Y.g0[y];
+            const T Pyz = Y.phi[y] * Z.phi[z];
+            const T Dyz = Y.dphi[y] * Z.phi[z] + Y.w[y] * Z.dphi[z];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                // rho phi_x phi_y phi_z - w_x w_y w_z = (dr phi_x + dphi_x) P_yz + w_x D_yz
+                const T ax = dr * X.phi[x] + X.dphi[x];
+                const T heq = ax * Pyz + X.w[x] * Dyz;
+                const T hne = B0 * X.g0[x] + B1 * X.g1[x] + B2 * X.g2[x];
+                h[dir_of(x - 1, y - 1, z - 1)] = heq + hne;
+            }
+        }
+    NodeMacro<T> out;
+    out.rho = rho;
+    out.ux = ux;
+    out.uy = uy;
+    out.uz = uz;
+    return out;
+}
+
+// Equilibrium deviations h^eq_a = f^eq_a(rho, u) - w_a (init and moving walls).
+template <class T>
+__device__ __forceinline__ void equilibrium_dev(T (&h)[Q], const Phys<T> &P, T rho, T ux, T uy, T uz)
+{
+    const AxisCols<T> X = axis_cols(ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0], P.cs2);
+    const AxisCols<T> Y = axis_cols(uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1], P.cs2);
+    const AxisCols<T> Z = axis_cols(uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2], P.cs2);
+    const T dr = rho - T(1);
+#pragma unroll
+    for (int y = 0; y < 3; ++y)
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+            const T Pyz = Y.phi[y] * Z.phi[z];
+            const T Dyz = Y.dphi[y] * Z.phi[z] + Y.w[y] * Z.dphi[z];
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                h[dir_of(x - 1, y - 1, z - 1)] = (dr * X.phi[x] + X.dphi[x]) * Pyz + X.w[x] * Dyz;
+        }
+}
+
+}  // namespace lbc

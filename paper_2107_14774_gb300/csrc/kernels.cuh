@@ -1,0 +1,366 @@
+// kernels.cuh -- CUDA kernels of liblbcuboid (templates; instantiated per storage
+// type in step_*.cu).
+//
+// State layout ("pull" convention).  The context stores S[27][N]: after a step,
+// S_a(x) holds the post-collision population f~_a(x, t) of node x itself.  The
+// pre-collision population of the next step is then obtained by streaming
+// (Sec. 3.2: f_a(x, t+1) = f~_a(x - e_a, t)) when it is read:
+//     f_a(x) = S_a(x - e_a)              if x - e_a is inside (periodic axes wrap)
+//     f_a(x) = S_opp(a)(x) + lid term    if x - e_a lies beyond a wall
+// (half-way bounce-back, Sec. 4).  Every stored value is read by exactly one
+// (node, direction) pair, so one fused kernel reads 27 and writes 27 values per
+// node and nothing else.
+#pragma once
+
+#include "collide.cuh"
+
+namespace lbc {
+
+constexpr int kBlockX = 32;   // threads along x per block
+constexpr int kBlockThreads = 128;
+
+// Source coordinates x - e of one node along each axis: index 0 for e = -1,
+// 1 for e = 0, 2 for e = +1.  out[] marks sources beyond a wall.
+struct Pull {
+    long long base;     // index of the node itself
+    int xs[3];          // x - e_x
+    long long yoff[3];  // (y - e_y) * nx
+    long long zoff[3];  // (z - e_z) * nx * ny
+    bool xo[3], yo[3], zo[3];
+};
+
+__device__ __forceinline__ void axis_sources(int c, int n, int wall, int (&src)[3], bool (&out)[3])
+{
+    // e = -1 -> c + 1, e = 0 -> c, e = +1 -> c - 1
+    int p = c + 1, m = c - 1;
+    out[0] = false;
+    out[1] = false;
+    out[2] = false;
+    if (p >= n) {
+        if (wall) out[0] = true;
+        p -= n;
+    }
+    if (m < 0) {
+        if (wall) out[2] = true;
+        m += n;
+    }
+    src[0] = p;
+    src[1] = c;
+    src[2] = m;
+}
+
+__device__ __forceinline__ Pull make_pull(const Geom &g, int i, int j, int k)
+{
+    Pull q;
+    int ys[3], zs[3];
+    axis_sources(i, g.nx, g.wall[0], q.xs, q.xo);
+    axis_sources(j, g.ny, g.wall[1], ys, q.yo);
+    axis_sources(k, g.nz, g.wall[2], zs, q.zo);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        q.yoff[t] = (long long)ys[t] * g.nx;
+        q.zoff[t] = (long long)zs[t] * g.nx * g.ny;
+    }
+    q.base = q.zoff[1] + q.yoff[1] + i;
+    return q;
+}
+
+// Storage offset read for direction a at this node.
+template <int A>
+__device__ __forceinline__ long long pull_offset(const Pull &q, long long N)
+{
+    constexpr int cx = ex(A) + 1, cy = ey(A) + 1, cz = ez(A) + 1;
+    const bool out = q.xo[cx] | q.yo[cy] | q.zo[cz];
+    const long long in_off = (long long)A * N + q.zoff[cz] + q.yoff[cy] + q.xs[cx];
+    const long long bb_off = (long long)opp(A) * N + q.base;
+    return out ? bb_off : in_off;
+}
+
+// Does direction a reach this node across the lid (the wall at j = ny - 1/2)?
+template <int A>
+__device__ __forceinline__ bool from_lid(const Pull &q)
+{
+    return ey(A) == -1 && q.yo[0];
+}
+
+template <int ST, int A>
+struct LoadDir {
+    using C = Codec<ST>;
+    using T = typename C::T;
+    static __device__ __forceinline__ void run(T (&h)[Q], const typename C::S *__restrict__ src,
+                                               const Pull &q, long long N, const DirConst<T> &D)
+    {
+        h[A] = C::load(__ldg(src + pull_offset<A>(q, N)), D.w[A], D.iscale[A]);
+        LoadDir<ST, A + 1>::run(h, src, q, N, D);
+    }
+};
+template <int ST>
+struct LoadDir<ST, Q> {
+    using C = Codec<ST>;
+    using T = typename C::T;
+    static __device__ __forceinline__ void run(T (&)[Q], const typename C::S *__restrict__, const Pull &,
+                                               long long, const DirConst<T> &) {}
+};
+
+// Pre-collision deviations h_a = f_a(x, t) - w_a of one node, streamed in.
+// With a moving lid the incoming links across it get the momentum-augmented
+// term -[f^eq_opp(a) - f^eq_a](rho_w, U) of Eq. momentumaugmentedBBscheme, with
+// the wall density taken as the fluid node's density sum_a S_a(x) (mass is
+// conserved by the collision, so this is rho(x, t-1)).
+template <int ST>
+__device__ __forceinline__ void pull_node(typename Codec<ST>::T (&h)[Q], const typename Codec<ST>::S *__restrict__ src,
+                                          const Pull &q, long long N, const DirConst<typename Codec<ST>::T> &D,
+                                          const Phys<typename Codec<ST>::T> &P, typename Codec<ST>::T lid_u)
+{
+    using C = Codec<ST>;
+    using T = typename C::T;
+    LoadDir<ST, 0>::run(h, src, q, N, D);
+    if (lid_u != T(0) && q.yo[0]) {
+        T rho_w = T(1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) rho_w += C::load(__ldg(src + (long long)a * N + q.base), D.w[a], D.iscale[a]);
+        // f^eq(rho_w, (U,0,0)): only the x factor depends on U; the correction
+        // f^eq_a - f^eq_opp(a) = rho_w phi_y phi_z (phi_x(ex) - phi_x(-ex)) = rho_w phi_y phi_z ex U
+        const AxisCols<T> Y = axis_cols(T(0), P.ic[1], P.ic2[1], P.w0[1], P.wpm[1], P.cs2);
+        const AxisCols<T> Z = axis_cols(T(0), P.ic[2], P.ic2[2], P.w0[2], P.wpm[2], P.cs2);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            if (ey(a) == -1 && ex(a) != 0) {
+                // incoming a, outgoing b = opp(a): f_a = f~_b - [f^eq_b - f^eq_a]
+                //                                      = f~_b + rho_w phi_y phi_z ex(a) U
+                h[a] += rho_w * Y.phi[ey(a) + 1] * Z.phi[ez(a) + 1] * T(ex(a)) * lid_u;
+            }
+        }
+    }
+}
+
+template <int ST, int CORR>
+__global__ void __launch_bounds__(kBlockThreads)
+k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__restrict__ dst, Geom g,
+       Phys<typename Codec<ST>::T> P, DirConst<typename Codec<ST>::T> D, typename Codec<ST>::T F0,
+       typename Codec<ST>::T F1, typename Codec<ST>::T F2, const typename Codec<ST>::T *__restrict__ ff,
+       const typename Codec<ST>::T *__restrict__ rho_field, typename Codec<ST>::T lid_u)
+{
+    using C = Codec<ST>;
+    using T = typename C::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const long long N = g.N;
+    const Pull q = make_pull(g, i, j, k);
+    T h[Q];
+    pull_node<ST>(h, src, q, N, D, P, lid_u);
+    T Fx = F0, Fy = F1, Fz = F2;
+    if (ff) {
+        Fx += __ldg(ff + q.base);
+        Fy += __ldg(ff + N + q.base);
+        Fz += __ldg(ff + 2 * N + q.base);
+    }
+    T grx = T(0), gry = T(0), grz = T(0);
+    if (CORR == LB_CORR_FULL) {
+        // second-order central differences of the current density; one-sided
+        // second-order differences next to a wall (spacings 1, r, s)
+        const int n[3] = {g.nx, g.ny, g.nz};
+        const int c[3] = {i, j, k};
+        const long long stride[3] = {1, (long long)g.nx, (long long)g.nx * g.ny};
+        T gr[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const T ih = P.ic[ax];
+            const long long x = q.base, st = stride[ax];
+            T d = T(0);
+            if (n[ax] == 1) {
+                d = T(0);
+            } else if (!g.wall[ax]) {
+                const long long xp = (c[ax] == n[ax] - 1) ? x - (long long)(n[ax] - 1) * st : x + st;
+                const long long xm = (c[ax] == 0) ? x + (long long)(n[ax] - 1) * st : x - st;
+                d = (__ldg(rho_field + xp) - __ldg(rho_field + xm)) * (T(0.5) * ih);
+            } else if (n[ax] == 2) {
+                d = (c[ax] == 0 ? __ldg(rho_field + x + st) - __ldg(rho_field + x)
+                                : __ldg(rho_field + x) - __ldg(rho_field + x - st)) * ih;
+            } else if (c[ax] == 0) {
+                d = (T(-3) * __ldg(rho_field + x) + T(4) * __ldg(rho_field + x + st) - __ldg(rho_field + x + 2 * st))
+                    * (T(0.5) * ih);
+            } else if (c[ax] == n[ax] - 1) {
+                d = (T(3) * __ldg(rho_field + x) - T(4) * __ldg(rho_field + x - st) + __ldg(rho_field + x - 2 * st))
+                    * (T(0.5) * ih);
+            } else {
+                d = (__ldg(rho_field + x + st) - __ldg(rho_field + x - st)) * (T(0.5) * ih);
+            }
+            gr[ax] = d;
+        }
+        grx = gr[0];
+        gry = gr[1];
+        grz = gr[2];
+    }
+    collide<T, CORR>(h, P, Fx, Fy, Fz, grx, gry, grz);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) dst[(long long)a * N + q.base] = C::store(h[a], D.w[a], D.scale[a]);
+}
+
+// Density of every node (pre-pass of LB_CORR_FULL).
+template <int ST>
+__global__ void __launch_bounds__(kBlockThreads)
+k_density(const typename Codec<ST>::S *__restrict__ src, Geom g, Phys<typename Codec<ST>::T> P,
+          DirConst<typename Codec<ST>::T> D, typename Codec<ST>::T lid_u, typename Codec<ST>::T *__restrict__ rho)
+{
+    using T = typename Codec<ST>::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const Pull q = make_pull(g, i, j, k);
+    T h[Q];
+    pull_node<ST>(h, src, q, g.N, D, P, lid_u);
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s += h[a];
+    rho[q.base] = T(1) + s;
+}
+
+// Density and velocity (Eq. 12) of every node; and/or the pre-collision
+// populations f_a = w_a + h_a.  Any output pointer may be null.
+template <int ST>
+__global__ void __launch_bounds__(kBlockThreads)
+k_gather(const typename Codec<ST>::S *__restrict__ src, Geom g, Phys<typename Codec<ST>::T> P,
+         DirConst<typename Codec<ST>::T> D, typename Codec<ST>::T F0, typename Codec<ST>::T F1,
+         typename Codec<ST>::T F2, const typename Codec<ST>::T *__restrict__ ff, typename Codec<ST>::T lid_u,
+         typename Codec<ST>::T *__restrict__ rho, typename Codec<ST>::T *__restrict__ u,
+         typename Codec<ST>::T *__restrict__ fout)
+{
+    using T = typename Codec<ST>::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const long long N = g.N;
+    const Pull q = make_pull(g, i, j, k);
+    T h[Q];
+    pull_node<ST>(h, src, q, N, D, P, lid_u);
+    if (fout) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) fout[(long long)a * N + q.base] = D.w[a] + h[a];
+    }
+    if (rho || u) {
+        const RawMoments<T> m = raw_moments(h, P);
+        T Fx = F0, Fy = F1, Fz = F2;
+        if (ff) {
+            Fx += ff[q.base];
+            Fy += ff[N + q.base];
+            Fz += ff[2 * N + q.base];
+        }
+        const T r = T(1) + m.dr;
+        if (rho) rho[q.base] = r;
+        if (u) {
+            u[q.base] = (m.jx + T(0.5) * Fx) / r;
+            u[N + q.base] = (m.jy + T(0.5) * Fy) / r;
+            u[2 * N + q.base] = (m.jz + T(0.5) * Fz) / r;
+        }
+    }
+}
+
+// Write pre-collision deviations h of node x into the pull layout (inverse of
+// pull_node, without lid terms): S_a(x - e_a) or, across a wall, S_opp(a)(x).
+template <int ST>
+__device__ __forceinline__ void scatter_node(const typename Codec<ST>::T (&h)[Q], typename Codec<ST>::S *__restrict__ dst,
+                                             const Pull &q, long long N, const DirConst<typename Codec<ST>::T> &D)
+{
+    using C = Codec<ST>;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
+        const bool out = q.xo[cx] | q.yo[cy] | q.zo[cz];
+        const long long off = out ? (long long)opp(a) * N + q.base
+                                  : (long long)a * N + q.zoff[cz] + q.yoff[cy] + q.xs[cx];
+        dst[off] = C::store(h[a], D.w[a], D.scale[a]);
+    }
+}
+
+// f := f^eq(rho, u) (init), or f := given populations (set).
+template <int ST>
+__global__ void __launch_bounds__(kBlockThreads)
+k_scatter(typename Codec<ST>::S *__restrict__ dst, Geom g, Phys<typename Codec<ST>::T> P,
+          DirConst<typename Codec<ST>::T> D, const typename Codec<ST>::T *__restrict__ rho,
+          const typename Codec<ST>::T *__restrict__ u, const typename Codec<ST>::T *__restrict__ fin)
+{
+    using T = typename Codec<ST>::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const long long N = g.N;
+    const Pull q = make_pull(g, i, j, k);
+    T h[Q];
+    if (fin) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) h[a] = fin[(long long)a * N + q.base] - D.w[a];
+    } else {
+        equilibrium_dev(h, P, rho[q.base], u[q.base], u[N + q.base], u[2 * N + q.base]);
+    }
+    scatter_node<ST>(h, dst, q, N, D);
+}
+
+// First pass of the FP64 reduction: per-block sums of rho and rho u (Eq. 12) in
+// a fixed tree order, plus a status bit for non-finite or non-positive density.
+constexpr int kReduceThreads = 256;
+
+template <int ST>
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce_partial(const typename Codec<ST>::S *__restrict__ src, Geom g, Phys<typename Codec<ST>::T> P,
+                 DirConst<typename Codec<ST>::T> D, typename Codec<ST>::T F0, typename Codec<ST>::T F1,
+                 typename Codec<ST>::T F2, const typename Codec<ST>::T *__restrict__ ff,
+                 typename Codec<ST>::T lid_u, double *__restrict__ partial, unsigned *__restrict__ status)
+{
+    using T = typename Codec<ST>::T;
+    __shared__ double sh[4][kReduceThreads];
+    const long long N = g.N;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    unsigned bad = 0;
+    // grid-stride over nodes in a fixed order
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % g.nx);
+        const long long t = n / g.nx;
+        const int j = (int)(t % g.ny);
+        const int k = (int)(t / g.ny);
+        const Pull q = make_pull(g, i, j, k);
+        T h[Q];
+        pull_node<ST>(h, src, q, N, D, P, lid_u);
+        const RawMoments<T> m = raw_moments(h, P);
+        T Fx = F0, Fy = F1, Fz = F2;
+        if (ff) {
+            Fx += ff[n];
+            Fy += ff[N + n];
+            Fz += ff[2 * N + n];
+        }
+        const double rho = 1.0 + (double)m.dr;
+        const double jx = (double)m.jx + 0.5 * (double)Fx;
+        const double jy = (double)m.jy + 0.5 * (double)Fy;
+        const double jz = (double)m.jz + 0.5 * (double)Fz;
+        if (!(rho > 0.0) || !isfinite(rho) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz)) bad = 1u;
+        acc[0] += rho;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] += jz;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) partial[4 * blockIdx.x + c] = sh[c][0];
+    if (bad) atomicOr(status, 1u);
+}
+
+// Second pass: one block sums the per-block partials in a fixed order.
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce_final(const double *__restrict__ partial, int nblocks, double *__restrict__ out);
+
+}  // namespace lbc

@@ -1,0 +1,449 @@
+// lbcuboid.cu -- C ABI of liblbcuboid (declared in include/lbcuboid.h): context
+// management, argument checking, host/device staging and dispatch to the
+// per-storage launchers of ops.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lbcuboid.h"
+#include "ops.cuh"
+
+using namespace lbc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lb_status fail(lb_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+lb_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+size_t storage_bytes(int st)
+{
+    switch (st) {
+    case LB_F64: return 8;
+    case LB_F32:
+    case LB_F32_SHIFTED: return 4;
+    default: return 2;
+    }
+}
+
+}  // namespace
+
+struct lb_ctx {
+    lb_config cfg;
+    Geom g;
+    double cs2, wn, wb;
+    double w[Q];
+    float scale[Q];
+    cudaStream_t stream;
+    void *buf[2];
+    int cur;
+    size_t sbytes;          // bytes of one stored value
+    size_t rbytes;          // bytes of one real
+    void *force_field;      // [3][N] real or null
+    void *rho_field;        // [N] real (FULL)
+    void *stage;            // staging for host pointers
+    size_t stage_bytes;
+    double *partial;
+    double *out4;
+    unsigned *status;
+    int nred;
+    long long t;
+    // True while the stored state holds pre-collision populations written by
+    // lb_init / lb_set_populations (the moving-lid term belongs to streaming after
+    // a collision, so it is not applied when those populations are read).
+    bool fresh;
+};
+
+namespace {
+
+LaunchArgs launch_args(const lb_ctx *c)
+{
+    LaunchArgs a;
+    a.g = c->g;
+    a.r = c->cfg.r_y;
+    a.s = c->cfg.r_z;
+    a.cs2 = c->cs2;
+    a.wn = c->wn;
+    a.wb = c->wb;
+    for (int i = 0; i < 3; ++i) a.F[i] = c->cfg.force[i];
+    a.lid_u = c->fresh ? 0.0 : c->cfg.lid_u;
+    for (int q = 0; q < Q; ++q) {
+        a.w[q] = c->w[q];
+        a.scale[q] = c->scale[q];
+    }
+    a.corr = c->cfg.corr;
+    a.stream = c->stream;
+    a.force_field = c->force_field;
+    a.rho_field = c->rho_field;
+    return a;
+}
+
+template <class F>
+cudaError_t dispatch(int st, F &&f)
+{
+    switch (st) {
+    case LB_F64: return f(Ops<LB_F64>());
+    case LB_F32: return f(Ops<LB_F32>());
+    case LB_F32_SHIFTED: return f(Ops<LB_F32_SHIFTED>());
+    case LB_F16_SHIFTED: return f(Ops<LB_F16_SHIFTED>());
+    default: return f(Ops<LB_BF16_SHIFTED>());
+    }
+}
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+lb_status ensure_stage(lb_ctx *c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return LB_OK;
+    if (c->stage) LB_CUDA(cudaFree(c->stage));
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    LB_CUDA(cudaMalloc(&c->stage, bytes));
+    c->stage_bytes = bytes;
+    return LB_OK;
+}
+
+// Device view of a caller input of `bytes` bytes placed at `offset` in the stage.
+lb_status device_input(lb_ctx *c, const void *p, size_t bytes, size_t offset, const void **dev)
+{
+    if (is_device_pointer(p)) {
+        *dev = p;
+        return LB_OK;
+    }
+    char *s = static_cast<char *>(c->stage) + offset;
+    LB_CUDA(cudaMemcpyAsync(s, p, bytes, cudaMemcpyHostToDevice, c->stream));
+    *dev = s;
+    return LB_OK;
+}
+
+// 1-D rest weight of velocity index v (-1, 0, 1) on an axis with speed c.
+double w1(int v, double c, double cs2) { return v == 0 ? 1.0 - cs2 / (c * c) : 0.5 * cs2 / (c * c); }
+
+}  // namespace
+
+extern "C" {
+
+void lb_config_default(lb_config *cfg, int nx, int ny, int nz, double r_y, double r_z, double nu)
+{
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = nx;
+    cfg->ny = ny;
+    cfg->nz = nz;
+    cfg->r_y = r_y;
+    cfg->r_z = r_z;
+    cfg->nu = nu;
+    cfg->zeta = 0.0;
+    cfg->cs2 = 0.0;
+    cfg->storage = LB_F32;
+    cfg->corr = LB_CORR_LOCAL;
+}
+
+lb_status lb_create(int nx, int ny, int nz, double r_y, double r_z, double nu, double zeta, lb_ctx **out)
+{
+    lb_config cfg;
+    lb_config_default(&cfg, nx, ny, nz, r_y, r_z, nu);
+    cfg.zeta = zeta;
+    return lb_create_ex(&cfg, out);
+}
+
+lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
+{
+    if (!cfg || !out) return fail(LB_EINVAL, "lb_create_ex: null argument");
+    *out = nullptr;
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(LB_EINVAL, "lb_create_ex: dimensions must be >= 1");
+    if (cfg->nz > 65535 || (cfg->ny + 127) / 128 > 65535)
+        return fail(LB_EINVAL, "lb_create_ex: ny or nz exceeds the launch-grid limit (nz <= 65535)");
+    if (!(cfg->r_y > 0.0) || !(cfg->r_z > 0.0) || !std::isfinite(cfg->r_y) || !std::isfinite(cfg->r_z))
+        return fail(LB_EINVAL, "lb_create_ex: aspect ratios must be positive and finite");
+    if (cfg->storage < LB_F64 || cfg->storage > LB_BF16_SHIFTED) return fail(LB_EINVAL, "lb_create_ex: bad storage");
+    if (cfg->corr < LB_CORR_NONE || cfg->corr > LB_CORR_FULL) return fail(LB_EINVAL, "lb_create_ex: bad corr");
+    if (cfg->wall_mask & ~7u) return fail(LB_EINVAL, "lb_create_ex: bad wall_mask");
+    if (cfg->lid_u != 0.0 && !(cfg->wall_mask & LB_WALL_Y))
+        return fail(LB_EINVAL, "lb_create_ex: a moving lid needs walls normal to y");
+    const double r = cfg->r_y, s = cfg->r_z;
+    const double cmin = std::fmin(1.0, std::fmin(r * r, s * s));
+    const double cs2 = cfg->cs2 > 0.0 ? cfg->cs2 : cmin / 3.0;
+    if (!(cs2 > 0.0) || !(cs2 < cmin))
+        return fail(LB_EINVAL, "lb_create_ex: cs2 must satisfy 0 < cs2 < min(1, r^2, s^2) (positive rest weights)");
+    if (!(cfg->nu > 0.0) || !std::isfinite(cfg->nu)) return fail(LB_EINVAL, "lb_create_ex: nu must be > 0");
+    const double wn = 1.0 / (cfg->nu / cs2 + 0.5);
+    const double wb = cfg->zeta > 0.0 ? 1.0 / (1.5 * cfg->zeta / cs2 + 0.5) : 1.0;
+    if (!(wn > 0.0 && wn < 2.0) || !(wb > 0.0 && wb < 2.0))
+        return fail(LB_EINVAL, "lb_create_ex: relaxation rates must lie in (0, 2)");
+    const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+
+    lb_ctx *c = new lb_ctx();
+    std::memset(static_cast<void *>(c), 0, sizeof(*c));
+    c->cfg = *cfg;
+    c->cfg.cs2 = cs2;
+    c->cs2 = cs2;
+    c->wn = wn;
+    c->wb = wb;
+    c->g.nx = cfg->nx;
+    c->g.ny = cfg->ny;
+    c->g.nz = cfg->nz;
+    for (int i = 0; i < 3; ++i) c->g.wall[i] = (cfg->wall_mask >> i) & 1u;
+    c->g.N = N;
+    c->stream = static_cast<cudaStream_t>(cfg->stream);
+    c->sbytes = storage_bytes(cfg->storage);
+    c->rbytes = cfg->storage == LB_F64 ? 8 : 4;
+    const double cc[3] = {1.0, r, s};
+    for (int a = 0; a < Q; ++a) {
+        const double wa = w1(ex(a), cc[0], cs2) * w1(ey(a), cc[1], cs2) * w1(ez(a), cc[2], cs2);
+        c->w[a] = wa;
+        // FP16: scale direction a by 2^E so that h_a / w_a ~ O(1) lands near 2^10,
+        // far from both the subnormal range and the 65504 limit.
+        c->scale[a] = cfg->storage == LB_F16_SHIFTED ? std::ldexp(1.0f, 10 - std::ilogb(wa)) : 1.0f;
+    }
+    const size_t bytes = (size_t)Q * N * c->sbytes;
+    cudaError_t e = cudaMalloc(&c->buf[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->buf[1], bytes);
+    c->nred = 2 * 152;
+    if (e == cudaSuccess) e = cudaMalloc(&c->partial, sizeof(double) * 4 * c->nred);
+    if (e == cudaSuccess) e = cudaMalloc(&c->out4, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(unsigned));
+    if (e == cudaSuccess && cfg->corr == LB_CORR_FULL) e = cudaMalloc(&c->rho_field, N * c->rbytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, bytes, c->stream);
+    if (e != cudaSuccess) {
+        lb_destroy(c);
+        return cuda_fail(e, "lb_create_ex: allocation");
+    }
+    *out = c;
+    return LB_OK;
+}
+
+void lb_destroy(lb_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->buf[0]);
+    cudaFree(c->buf[1]);
+    cudaFree(c->force_field);
+    cudaFree(c->rho_field);
+    cudaFree(c->stage);
+    cudaFree(c->partial);
+    cudaFree(c->out4);
+    cudaFree(c->status);
+    delete c;
+}
+
+int lb_real_size(const lb_ctx *c) { return c ? (int)c->rbytes : 0; }
+
+size_t lb_num_nodes(const lb_ctx *c) { return c ? (size_t)c->g.N : 0; }
+
+lb_status lb_get_params(const lb_ctx *c, double out[3])
+{
+    if (!c || !out) return fail(LB_EINVAL, "lb_get_params: null argument");
+    out[0] = c->wn;
+    out[1] = c->wb;
+    out[2] = c->cs2;
+    return LB_OK;
+}
+
+long long lb_time_step(const lb_ctx *c) { return c ? c->t : -1; }
+
+lb_status lb_init(lb_ctx *c, const void *rho, const void *u)
+{
+    if (!c || !rho || !u) return fail(LB_EINVAL, "lb_init: null argument");
+    const size_t nb = (size_t)c->g.N * c->rbytes;
+    lb_status st = LB_OK;
+    if (!is_device_pointer(rho) || !is_device_pointer(u)) st = ensure_stage(c, 4 * nb);
+    if (st) return st;
+    const void *drho, *du;
+    if ((st = device_input(c, rho, nb, 0, &drho))) return st;
+    if ((st = device_input(c, u, 3 * nb, nb, &du))) return st;
+    const LaunchArgs a = launch_args(c);
+    void *dst = c->buf[c->cur];
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::scatter(a, dst, drho, du, nullptr); }));
+    c->t = 0;
+    c->fresh = true;
+    return LB_OK;
+}
+
+lb_status lb_set_force_field(lb_ctx *c, const void *force)
+{
+    if (!c) return fail(LB_EINVAL, "lb_set_force_field: null context");
+    const size_t nb = 3 * (size_t)c->g.N * c->rbytes;
+    if (!force) {
+        LB_CUDA(cudaStreamSynchronize(c->stream));
+        LB_CUDA(cudaFree(c->force_field));
+        c->force_field = nullptr;
+        return LB_OK;
+    }
+    if (!c->force_field) LB_CUDA(cudaMalloc(&c->force_field, nb));
+    LB_CUDA(cudaMemcpyAsync(c->force_field, force, nb, cudaMemcpyDefault, c->stream));
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx *c, int n)
+{
+    if (!c) return fail(LB_EINVAL, "lb_step: null context");
+    if (n < 0) return fail(LB_EINVAL, "lb_step: n must be >= 0");
+    for (int i = 0; i < n; ++i) {
+        const LaunchArgs a = launch_args(c);
+        const void *src = c->buf[c->cur];
+        void *dst = c->buf[c->cur ^ 1];
+        LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); }));
+        c->cur ^= 1;
+        ++c->t;
+        c->fresh = false;
+    }
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_ctx *c, void *rho, void *u)
+{
+    if (!c || (!rho && !u)) return fail(LB_EINVAL, "lb_moments: null argument");
+    const size_t nb = (size_t)c->g.N * c->rbytes;
+    const bool dr = !rho || is_device_pointer(rho), du = !u || is_device_pointer(u);
+    if (!dr || !du) {
+        lb_status st = ensure_stage(c, 4 * nb);
+        if (st) return st;
+    }
+    char *stage = static_cast<char *>(c->stage);
+    void *trho = rho ? (dr ? rho : stage) : nullptr;
+    void *tu = u ? (du ? u : stage + nb) : nullptr;
+    const LaunchArgs a = launch_args(c);
+    const void *src = c->buf[c->cur];
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::gather(a, src, trho, tu, nullptr); }));
+    if (rho && !dr) LB_CUDA(cudaMemcpyAsync(rho, trho, nb, cudaMemcpyDeviceToHost, c->stream));
+    if (u && !du) LB_CUDA(cudaMemcpyAsync(u, tu, 3 * nb, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_reduce(lb_ctx *c, double out[4])
+{
+    if (!c || !out) return fail(LB_EINVAL, "lb_reduce: null argument");
+    const LaunchArgs a = launch_args(c);
+    const void *src = c->buf[c->cur];
+    LB_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) {
+        return decltype(ops)::reduce_partial(a, src, c->partial, c->nred, c->status);
+    }));
+    k_reduce_final<<<1, kReduceThreads, 0, c->stream>>>(c->partial, c->nred, c->out4);
+    LB_CUDA(cudaGetLastError());
+    unsigned status = 0;
+    LB_CUDA(cudaMemcpyAsync(out, c->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    if (status) return fail(LB_EUNSTABLE, "lb_reduce: non-finite or non-positive density/velocity found");
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_ctx *c, void *dst)
+{
+    if (!c || !dst) return fail(LB_EINVAL, "lb_get_populations: null argument");
+    const size_t nb = (size_t)Q * c->g.N * c->rbytes;
+    const bool dev = is_device_pointer(dst);
+    if (!dev) {
+        lb_status st = ensure_stage(c, nb);
+        if (st) return st;
+    }
+    void *t = dev ? dst : c->stage;
+    const LaunchArgs a = launch_args(c);
+    const void *src = c->buf[c->cur];
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::gather(a, src, nullptr, nullptr, t); }));
+    if (!dev) LB_CUDA(cudaMemcpyAsync(dst, t, nb, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_ctx *c, const void *src)
+{
+    if (!c || !src) return fail(LB_EINVAL, "lb_set_populations: null argument");
+    const size_t nb = (size_t)Q * c->g.N * c->rbytes;
+    const bool dev = is_device_pointer(src);
+    if (!dev) {
+        lb_status st = ensure_stage(c, nb);
+        if (st) return st;
+    }
+    const void *dsrc;
+    lb_status st = device_input(c, src, nb, 0, &dsrc);
+    if (st) return st;
+    const LaunchArgs a = launch_args(c);
+    void *dst = c->buf[c->cur];
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::scatter(a, dst, nullptr, nullptr, dsrc); }));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    c->t = 0;
+    c->fresh = true;
+    return LB_OK;
+}
+
+size_t lb_state_bytes(const lb_ctx *c) { return c ? (size_t)Q * c->g.N * c->sbytes : 0; }
+
+lb_status lb_get_state(lb_ctx *c, void *dst)
+{
+    if (!c || !dst) return fail(LB_EINVAL, "lb_get_state: null argument");
+    LB_CUDA(cudaMemcpyAsync(dst, c->buf[c->cur], lb_state_bytes(c), cudaMemcpyDefault, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_state(lb_ctx *c, const void *src, long long time_step)
+{
+    if (!c || !src) return fail(LB_EINVAL, "lb_set_state: null argument");
+    LB_CUDA(cudaMemcpyAsync(c->buf[c->cur], src, lb_state_bytes(c), cudaMemcpyDefault, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    c->t = time_step;
+    c->fresh = false;
+    return LB_OK;
+}
+
+const char *lb_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+namespace lbc {
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_reduce_final(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
+{
+    __shared__ double sh[4][kReduceThreads];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += partial[4 * b + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out[c] = sh[c][0];
+}
+
+}  // namespace lbc

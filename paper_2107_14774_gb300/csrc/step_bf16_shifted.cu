@@ -1,0 +1,4 @@
+// Instantiation of the kernels and launchers for population storage LB_BF16_SHIFTED.
+#include "ops.cuh"
+
+template struct lbc::Ops<LB_BF16_SHIFTED>;

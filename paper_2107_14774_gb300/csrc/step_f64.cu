@@ -1,0 +1,4 @@
+// Instantiation of the kernels and launchers for population storage LB_F64.
+#include "ops.cuh"
+
+template struct lbc::Ops<LB_F64>;

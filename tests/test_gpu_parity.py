@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.  FP64 storage: <= 1e-12 relative; FP32: <= 1e-5 relative on rho and
+u (relative error = ||a - b||_2 / ||b||_2)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_pair(oracle_mod, n, r, s, nu, cs2=None, corr="local", walls="", force=(0.0, 0.0, 0.0), storage="f64",
+              zeta=0.0, lid_u=0.0, force_field=None):
+    from paper_2107_14774_gb300 import Lattice
+    lat = Lattice(*n, r_y=r, r_z=s, nu=nu, zeta=zeta, cs2=cs2 or 0.0, storage=storage, corr=corr, walls=walls,
+                  force=force, lid_u=lid_u)
+    p = lat.params
+    o = oracle_mod.Oracle(*n, r=r, s=s, cs2=p["cs2"], omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
+                          corr=getattr(oracle_mod, "CORR_" + corr.upper()), walls=walls, force=force,
+                          force_field=force_field, lid_u=lid_u)
+    if force_field is not None:
+        lat.set_force_field(torch.from_numpy(force_field).cuda())
+    return lat, o
+
+
+def run_both(lat, o, rho, u, steps):
+    lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    lat.step(steps)
+    f_gpu = lat.populations().cpu().numpy()
+    rg, ug = (t.cpu().numpy() for t in lat.moments())
+    f_ref = o.run(o.init(rho, u), steps)
+    rr, ur = o.moments(f_ref)
+    return f_gpu, f_ref, rg, ug, rr, ur
+
+
+@pytest.mark.parametrize("corr", ["none", "lowmach", "local", "full"])
+@pytest.mark.parametrize("n,r,s,walls", [
+    ((37, 12, 9), 0.5, 2.0, ""),          # ragged x (not a multiple of the 32-wide block)
+    ((20, 12, 9), 1.0, 0.5, "y"),         # channel walls
+    ((16, 10, 12), 0.5, 1.0, "yz"),       # duct walls
+    ((9, 7, 6), 0.406, 1.3, "xyz"),       # closed box, corners and edges
+    ((1, 24, 16), 0.25, 1.0, "y"),        # degenerate x axis
+])
+def test_fp64_parity_small(oracle_mod, corr, n, r, s, walls):
+    rho, u = synth.solenoidal_random(*n, r, s, 2.0, 0.03, seed=11)
+    rho = rho + 0.002 * np.cos(2 * np.pi * np.arange(n[0]) / max(n[0], 2))[None, None, :]
+    F = (2e-5, -1e-5, 5e-6)
+    lat, o = make_pair(oracle_mod, n, r, s, 0.02, corr=corr, walls=walls, force=F, zeta=0.01)
+    f_gpu, f_ref, rg, ug, rr, ur = run_both(lat, o, rho, u, 6)
+    assert rel(f_gpu, f_ref) < TOL64
+    assert rel(rg, rr) < TOL64 and rel(ug, ur) < TOL64
+    lat.close()
+
+
+def test_fp64_parity_force_field(oracle_mod):
+    n, r, s = (24, 16, 8), 1.0, 0.5
+    ff = synth.force_field(*n, 1e-5, seed=44)
+    rho, u = synth.solenoidal_random(*n, r, s, 4.0, 0.01, seed=4)
+    lat, o = make_pair(oracle_mod, n, r, s, 0.01, force_field=ff)
+    f_gpu, f_ref, *_ = run_both(lat, o, rho, u, 5)
+    assert rel(f_gpu, f_ref) < TOL64
+    lat.close()
+
+
+def test_config1_taylor_green_fp64_full_run(oracle_mod):
+    """32x32x16, r=1, s=0.5, nu=0.01, u0=0.02, FP64, 100 steps: fields within 1e-12 of the
+    oracle; mass conserved to 1e-13 and total momentum zero."""
+    n, r, s = (32, 32, 16), 1.0, 0.5
+    rho, u, _ = synth.taylor_green_3d(*n, r, s, 0.02)
+    lat, o = make_pair(oracle_mod, n, r, s, 0.01)
+    m0 = lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).reduce()
+    lat.step(100)
+    m1 = lat.reduce()
+    rg, ug = (t.cpu().numpy() for t in lat.moments())
+    rr, ur = o.moments(o.run(o.init(rho, u), 100))
+    assert rel(rg, rr) < TOL64 and rel(ug, ur) < TOL64
+    assert abs(m1[0] / m0[0] - 1) < 1e-13
+    assert np.abs(m1[1:]).max() < 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", TOL64), ("f32", TOL32), ("f32s", TOL32)])
+def test_config2_duct_parity(oracle_mod, storage, tol):
+    """16x64x128 duct, r=0.5, s=2, walls y/z, F=1e-6 from rest plus a small seeded
+    solenoidal disturbance (so that every velocity component is exercised): 300 steps
+    against the oracle."""
+    n, r, s, cs2 = (16, 64, 128), 0.5, 2.0, 1 / 12
+    rho, u = np.ones(n[::-1]), np.zeros((3,) + n[::-1])
+    lat, o = make_pair(oracle_mod, n, r, s, cs2 / 2, cs2=cs2, walls="yz", force=(1e-6, 0.0, 0.0), storage=storage)
+    _, up = synth.solenoidal_random(*n, r, s, 3.0, 0.01, seed=2)
+    f_gpu, f_ref, rg, ug, rr, ur = run_both(lat, o, rho, u + up, 300)
+    assert rel(rg, rr) < tol
+    assert rel(ug, ur) < tol
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_config2_duct_converges_to_series(storage):
+    """Full config-2 run (20k steps) on the GPU against the rectangular-duct series (Eq. 70
+    generalised), 2a = ny r = 32, 2b = nz s = 256."""
+    from paper_2107_14774_gb300 import Lattice
+    from tests.analytic import duct_series
+    n, r, s, cs2 = (16, 64, 128), 0.5, 2.0, 1 / 12
+    nu, Fx = cs2 / 2, 1e-6
+    lat = Lattice(*n, r_y=r, r_z=s, nu=nu, cs2=cs2, storage=storage, walls="yz", force=(Fx, 0, 0))
+    lat.init(torch.ones(n[::-1]).cuda(), torch.zeros((3,) + n[::-1]).cuda()).step(20000)
+    _, u = lat.moments()
+    ux = u[0].mean(dim=2).cpu().numpy().astype(np.float64)    # average over x: [nz, ny]
+    a, b = n[1] * r / 2, n[2] * s / 2
+    Z, Y = np.meshgrid((np.arange(n[2]) + 0.5) * s - b, (np.arange(n[1]) + 0.5) * r - a, indexing="ij")
+    ua = duct_series(Y, Z, a, b, Fx, 1.0, nu)
+    assert rel(ux, ua) < 0.01
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f32s", 1e-5), ("f16s", 1e-3), ("bf16s", 6e-3)])
+def test_reduced_precision_storage_short_run(oracle_mod, storage, tol):
+    """Shifted FP16/BF16 storage against the FP64 oracle after a few steps: the stored
+    deviations carry 11 (FP16) / 8 (BF16) significant bits."""
+    n, r, s = (40, 24, 24), 0.5, 0.5
+    rho, u = synth.solenoidal_random(*n, r, s, 4.0, 0.03, seed=3)
+    lat, o = make_pair(oracle_mod, n, r, s, 0.005, storage=storage)
+    f_gpu, f_ref, rg, ug, rr, ur = run_both(lat, o, rho, u, 10)
+    assert rel(ug, ur) < tol
+    assert rel(rg - 1, rr - 1) < 20 * tol
+    lat.close()
+
+
+def test_full_size_config3_sampled_nodes(oracle_mod):
+    """512x256x256 (config 3), FP32 storage, one fused step from the seeded solenoidal
+    field: sampled nodes (and all 27 populations) against the oracle, which computes
+    each sampled node's 27 upstream collisions one by one from the same inputs."""
+    from paper_2107_14774_gb300 import Lattice
+    n, r, s, cs2, nu = (512, 256, 256), 0.5, 0.5, 1 / 12, 0.005
+    rho, u = synth.solenoidal_random(*n, r, s, 4.0, 0.03, seed=3)
+    lat = Lattice(*n, r_y=r, r_z=s, nu=nu, cs2=cs2, storage="f32")
+    lat.init(torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+    m0 = lat.reduce()
+    lat.step(1)
+    m1 = lat.reduce()
+    f = lat.populations()
+    p = lat.params
+    o = oracle_mod.Oracle(r=r, s=s, cs2=cs2, omega_nu=p["omega_nu"], omega_xi=p["omega_xi"])
+    e = o.velocities()
+    rng = np.random.default_rng(0)
+    pts = [(0, 0, 0), (n[0] - 1, n[1] - 1, n[2] - 1), (31, 32, 255)] + [
+        tuple(int(rng.integers(0, m)) for m in n) for _ in range(12)]
+    rho32, u32 = rho.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    worst = 0.0
+    for (i, j, k) in pts:
+        got = f[:, k, j, i].cpu().numpy().astype(np.float64)
+        want = np.empty(27)
+        for a in range(27):
+            ii, jj, kk = (i - e[0, a]) % n[0], (j - e[1, a]) % n[1], (k - e[2, a]) % n[2]
+            feq = o.equilibrium(rho32[kk, jj, ii], u32[:, kk, jj, ii])
+            want[a] = o.collide_node(feq)[a]
+        worst = max(worst, np.abs(got - want).max() / np.abs(want).max())
+    assert worst < 2e-6
+    assert abs(m1[0] / m0[0] - 1) < 1e-6
+    lat.close()
+
+
+def test_state_checkpoint_resume_is_bit_exact():
+    from paper_2107_14774_gb300 import Lattice
+    n = (24, 16, 8)
+    rho, u = synth.solenoidal_random(*n, 1.0, 0.5, 3.0, 0.02, seed=9)
+    for storage in ["f32", "bf16s", "f16s"]:
+        a = Lattice(*n, r_y=1.0, r_z=0.5, nu=0.01, storage=storage, walls="z")
+        b = Lattice(*n, r_y=1.0, r_z=0.5, nu=0.01, storage=storage, walls="z")
+        a.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(7)
+        st = a.get_state().cpu()
+        a.step(5)
+        b.set_state(st.cuda(), 7).step(5)
+        assert torch.equal(a.get_state(), b.get_state())
+        assert b.time_step == 12
+        a.close()
+        b.close()
+
+
+def test_host_and_device_pointers_agree():
+    from paper_2107_14774_gb300 import Lattice
+    n = (16, 8, 8)
+    rho, u = synth.solenoidal_random(*n, 0.5, 0.5, 3.0, 0.02, seed=1)
+    a = Lattice(*n, r_y=0.5, r_z=0.5, nu=0.01)
+    b = Lattice(*n, r_y=0.5, r_z=0.5, nu=0.01)
+    a.init(torch.from_numpy(rho).float().cuda(), torch.from_numpy(u).float().cuda()).step(3)
+    b.init(torch.from_numpy(rho).float(), torch.from_numpy(u).float().pin_memory()).step(3)
+    ra, ua = a.moments()
+    rb = torch.empty(n[::-1]).pin_memory()
+    ub = torch.empty((3,) + n[::-1])
+    b.moments(rb, ub)
+    assert torch.equal(ra.cpu(), rb) and torch.equal(ua.cpu(), ub)
+    a.close()
+    b.close()
+
+
+def test_set_populations_roundtrip(oracle_mod):
+    from paper_2107_14774_gb300 import Lattice
+    n = (12, 10, 8)
+    rho, u = synth.solenoidal_random(*n, 0.5, 1.0, 3.0, 0.02, seed=5)
+    lat, o = make_pair(oracle_mod, n, 0.5, 1.0, 0.02, walls="xz")
+    f0 = o.init(rho, u)
+    lat.set_populations(torch.from_numpy(f0).cuda())
+    np.testing.assert_array_equal(lat.populations().cpu().numpy(), f0)
+    lat.step(4)
+    assert rel(lat.populations().cpu().numpy(), o.run(f0, 4)) < TOL64
+    lat.close()
+
+
+def test_moving_lid_parity(oracle_mod):
+    """Lid-driven box (walls on every axis, lid at the top y wall), FP64, 30 steps."""
+    n, r, s = (10, 12, 8), 0.5, 0.75
+    rho, u = np.ones(n[::-1]), np.zeros((3,) + n[::-1])
+    lat, o = make_pair(oracle_mod, n, r, s, 0.02, cs2=0.04, walls="xyz", lid_u=0.05)
+    f_gpu, f_ref, *_ = run_both(lat, o, rho, u, 30)
+    assert rel(f_gpu, f_ref) < TOL64
+    lat.close()
+
+
+def test_unstable_state_is_reported():
+    """A NaN planted in the initial density is reported by lb_reduce as LB_EUNSTABLE."""
+    from paper_2107_14774_gb300 import Lattice, LBError
+    n = (8, 8, 8)
+    rho = np.ones(n[::-1])
+    rho[3, 4, 5] = np.nan
+    lat = Lattice(*n, nu=0.02)
+    lat.init(torch.from_numpy(rho).cuda(), torch.zeros((3,) + n[::-1]).cuda()).step(2)
+    with pytest.raises(LBError, match="EUNSTABLE"):
+        lat.reduce()
+    sums = lat.reduce(allow_unstable=True)
+    assert np.isnan(sums[0])
+    lat.close()
