@@ -96,6 +96,8 @@ typedef struct {
     double lid_u;          /* velocity along x of the wall at j = ny - 1/2 (needs LB_WALL_Y);
                               momentum-augmented bounce-back (Sec. 4, Eq. 69); 0 = at rest */
     void *stream;          /* cudaStream_t to issue all work on; NULL = the legacy default stream */
+    int kernel;            /* 0: automatic (two nodes per thread where the lattice allows it);
+                              1: always one node per thread (for cross-checks) */
 } lb_config;
 
 /* Fill *cfg with defaults: FP32 storage, LOCAL corrections, periodic, no

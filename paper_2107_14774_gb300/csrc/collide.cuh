@@ -6,61 +6,86 @@
 // in their separable one-dimensional form: the monomial basis {1, e, e^2} per
 // axis and the three velocities {-c, 0, c} per axis make P, S and F(u) tensor
 // products of 3x3 factors, so the 27x27 products of Apps. A-C and E-G reduce to
-// nine 3-point transforms per axis.  Because every relaxation rate other than
-// omega_nu and omega_xi is 1 (App. D), the post-collision central moments equal
-// their Maxwellian equilibria (Eq. 9) except
+// 3-point transforms along one axis at a time.  Because every relaxation rate
+// other than omega_nu and omega_xi is 1 (App. D), the post-collision central
+// moments equal their Maxwellian equilibria (Eq. 9) except
 //   k~_100 = F_x / 2 (and y, z),  k~_110 = (1 - omega_nu) k_110 (and 101, 011),
 //   the three diagonal second-order moments (relaxed via B, B^-1 with the
 //   corrected equilibria of Eq. 63 / App. D);
 // so only the ten raw moments of order <= 2 are needed on the way in, and on the
 // way out f~ = f^eq(rho, u) + M(u)^-1 (k~ - k^eq), where the second term has only
 // nine non-zero central-moment inputs.
+//
+// The code is generic in the lane type V: float or double for one node per
+// thread, or F2 (two nodes per thread in the packed FP32x2 instructions of
+// sm_100+) for the linear transforms around the per-node scalar collision.
 #pragma once
 
 #include "lattice.cuh"
 
 namespace lbc {
 
+// Two FP32 lanes evaluated with the packed FFMA2/FADD2/FMUL2 instructions.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float c) : v(make_float2(c, c)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2 &operator-=(F2 &a, F2 b) { return a = a - b; }
+
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+template <class V> struct Scalar { using type = V; };
+template <> struct Scalar<F2> { using type = float; };
+
 // Per-axis columns of the inverse central-moment transform M(u)^-1 for one axis
 // with speed c and velocity u (velocity index v = -1, 0, +1 -> [0], [1], [2]):
 // the 1-D populations whose central moments about u are (1,0,0), (0,1,0),
 // (0,0,1).  Raw moments (1, u, u^2), (0, 1, 2u), (0, 0, 1) mapped to the three
 // velocities by g(0) = M0 - M2/c^2, g(+-c) = (M2/c^2 +- M1/c)/2.
-template <class T>
+template <class V>
 struct AxisCols {
-    T g0[3], g1[3], g2[3];  // columns for central moments of order 0, 1, 2
-    T phi[3], dphi[3];      // equilibrium factor phi = g0 + cs2 g2 and phi - w
-    T w[3];                 // 1-D rest weights
+    V g0[3], g1[3], g2[3];  // columns for central moments of order 0, 1, 2
+    V phi[3], dphi[3];      // equilibrium factor phi = g0 + cs2 g2 and phi - w
+    V w[3];                 // 1-D rest weights
 };
 
-template <class T>
-__device__ __forceinline__ AxisCols<T> axis_cols(T u, T ic, T ic2, T w0, T wpm, T cs2)
+template <class V, class T>
+__device__ __forceinline__ AxisCols<V> axis_cols(V u, T ic, T ic2, T w0, T wpm)
 {
-    AxisCols<T> A;
-    const T a = u * ic;        // u / c
-    const T b = a * a;         // u^2 / c^2
-    const T hb = T(0.5) * b, ha = T(0.5) * a;
+    AxisCols<V> A;
+    const V a = u * V(ic);       // u / c
+    const V b = a * a;           // u^2 / c^2
+    const V hb = V(T(0.5)) * b, ha = V(T(0.5)) * a;
     A.g0[0] = hb - ha;
-    A.g0[1] = T(1) - b;
+    A.g0[1] = V(T(1)) - b;
     A.g0[2] = hb + ha;
-    const T hic = T(0.5) * ic;
-    const T aic = a * ic;      // u / c^2
+    const V hic = V(T(0.5) * ic);
+    const V aic = a * V(ic);     // u / c^2
     A.g1[0] = aic - hic;
-    A.g1[1] = T(-2) * aic;
+    A.g1[1] = V(T(-2)) * aic;
     A.g1[2] = aic + hic;
-    A.g2[0] = T(0.5) * ic2;
-    A.g2[1] = -ic2;
-    A.g2[2] = T(0.5) * ic2;
+    A.g2[0] = V(T(0.5) * ic2);
+    A.g2[1] = V(-ic2);
+    A.g2[2] = V(T(0.5) * ic2);
     A.dphi[0] = A.g0[0];
     A.dphi[1] = -b;
     A.dphi[2] = A.g0[2];
-    A.w[0] = wpm;
-    A.w[1] = w0;
-    A.w[2] = wpm;
-    A.phi[0] = wpm + A.dphi[0];
-    A.phi[1] = w0 + A.dphi[1];
-    A.phi[2] = wpm + A.dphi[2];
-    (void)cs2;
+    A.w[0] = V(wpm);
+    A.w[1] = V(w0);
+    A.w[2] = V(wpm);
+    A.phi[0] = V(wpm) + A.dphi[0];
+    A.phi[1] = V(w0) + A.dphi[1];
+    A.phi[2] = V(wpm) + A.dphi[2];
     return A;
 }
 
@@ -73,35 +98,35 @@ struct NodeMacro {
 // Pre-collision moments of order <= 2 of one node, from the deviations h.
 // Cubic raw moments are summed along x-lines, then y, then z (App. A in
 // separable form); the cuboid scaling S (Eq. 59, App. B) follows.
-template <class T>
+template <class V>
 struct RawMoments {
-    T dr;                      // sum h   (rho - 1)
-    T jx, jy, jz;              // sum h e (cuboid e)
-    T pxx, pyy, pzz, pxy, pxz, pyz;  // sum h e_i e_j
+    V dr;                      // sum h   (rho - 1)
+    V jx, jy, jz;              // sum h e (cuboid e)
+    V pxx, pyy, pzz, pxy, pxz, pyz;  // sum h e_i e_j
 };
 
-template <class T>
-__device__ __forceinline__ RawMoments<T> raw_moments(const T (&h)[Q], const Phys<T> &P)
+template <class V, class T>
+__device__ __forceinline__ RawMoments<V> raw_moments(const V (&h)[Q], const Phys<T> &P)
 {
     // x-lines: for each (ey, ez) the sums over ex of h, h ex, h ex^2
-    T X0[3][3], X1[3][3], X2[3][3];
+    V X0[3][3], X1[3][3], X2[3][3];
 #pragma unroll
     for (int jy = 0; jy < 3; ++jy)
 #pragma unroll
         for (int jz = 0; jz < 3; ++jz) {
-            const T hm = h[dir_of(-1, jy - 1, jz - 1)];
-            const T h0 = h[dir_of(0, jy - 1, jz - 1)];
-            const T hp = h[dir_of(1, jy - 1, jz - 1)];
-            const T t = hp + hm;
+            const V hm = h[dir_of(-1, jy - 1, jz - 1)];
+            const V h0 = h[dir_of(0, jy - 1, jz - 1)];
+            const V hp = h[dir_of(1, jy - 1, jz - 1)];
+            const V t = hp + hm;
             X0[jy][jz] = t + h0;
             X1[jy][jz] = hp - hm;
             X2[jy][jz] = t;
         }
     // y stage (only the combinations of total order <= 2 are kept)
-    T Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
+    V Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
 #pragma unroll
     for (int jz = 0; jz < 3; ++jz) {
-        const T s = X0[2][jz] + X0[0][jz];
+        const V s = X0[2][jz] + X0[0][jz];
         Y00[jz] = s + X0[1][jz];
         Y01[jz] = X0[2][jz] - X0[0][jz];
         Y02[jz] = s;
@@ -109,43 +134,58 @@ __device__ __forceinline__ RawMoments<T> raw_moments(const T (&h)[Q], const Phys
         Y11[jz] = X1[2][jz] - X1[0][jz];
         Y20[jz] = X2[0][jz] + X2[1][jz] + X2[2][jz];
     }
-    RawMoments<T> m;
-    const T s00 = Y00[2] + Y00[0];
+    RawMoments<V> m;
+    const V s00 = Y00[2] + Y00[0];
     m.dr = s00 + Y00[1];
-    const T m001 = Y00[2] - Y00[0];
-    const T m002 = s00;
-    const T m010 = Y01[0] + Y01[1] + Y01[2];
-    const T m011 = Y01[2] - Y01[0];
-    const T m020 = Y02[0] + Y02[1] + Y02[2];
-    const T m100 = Y10[0] + Y10[1] + Y10[2];
-    const T m101 = Y10[2] - Y10[0];
-    const T m110 = Y11[0] + Y11[1] + Y11[2];
-    const T m200 = Y20[0] + Y20[1] + Y20[2];
+    const V m001 = Y00[2] - Y00[0];
+    const V m002 = s00;
+    const V m010 = Y01[0] + Y01[1] + Y01[2];
+    const V m011 = Y01[2] - Y01[0];
+    const V m020 = Y02[0] + Y02[1] + Y02[2];
+    const V m100 = Y10[0] + Y10[1] + Y10[2];
+    const V m101 = Y10[2] - Y10[0];
+    const V m110 = Y11[0] + Y11[1] + Y11[2];
+    const V m200 = Y20[0] + Y20[1] + Y20[2];
     // S: scale by r^n s^p (Eq. 59)
     const T r = P.c[1], s = P.c[2];
     m.jx = m100;
-    m.jy = r * m010;
-    m.jz = s * m001;
+    m.jy = V(r) * m010;
+    m.jz = V(s) * m001;
     m.pxx = m200;
-    m.pyy = (r * r) * m020;
-    m.pzz = (s * s) * m002;
-    m.pxy = r * m110;
-    m.pxz = s * m101;
-    m.pyz = (r * s) * m011;
+    m.pyy = V(r * r) * m020;
+    m.pzz = V(s * s) * m002;
+    m.pxy = V(r) * m110;
+    m.pxz = V(s) * m101;
+    m.pyz = V(r * s) * m011;
     return m;
 }
 
-// One collision, in place on the deviations h (Sec. 3.2 steps, App. D).
-// F: body force at the node; gr: density gradient (used by LB_CORR_FULL only).
+// Post-collision central moments of one node that differ from the Maxwellian
+// equilibrium (deviations), plus the hydrodynamic state.
+template <class V>
+struct PostState {
+    V dr, ux, uy, uz;           // rho - 1, velocity (with F/2, Eq. 12)
+    V hFx, hFy, hFz;            // k~_100 = F/2 (omega_1 = 1)
+    V t110, t101, t011;         // (1 - omega_nu) k_1..
+    V d200, d020, d002;         // k~_200 - cs2 rho, ...
+};
+
+// Division used by the per-node collision: IEEE for double; for float a
+// correctly rounded reciprocal times the numerator (the quantities divided are
+// O(u^2) corrections and the density, well inside the FP32 error budget).
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_(float a, float b) { return a * __frcp_rn(b); }
+
+// Relaxation of one node (App. D) from its raw moments.  F: body force at the
+// node; gr: density gradient (used by LB_CORR_FULL only).
 template <class T, int CORR>
-__device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T Fx, T Fy, T Fz,
-                                                T grx = T(0), T gry = T(0), T grz = T(0))
+__device__ __forceinline__ PostState<T> relax_node(const RawMoments<T> &m, const Phys<T> &P, T Fx, T Fy, T Fz,
+                                                   T grx, T gry, T grz)
 {
-    const RawMoments<T> m = raw_moments(h, P);
     const T cs2 = P.cs2;
     const T dr = m.dr;
     const T rho = T(1) + dr;
-    const T irho = T(1) / rho;
+    const T irho = div_(T(1), rho);
     // rho u = sum f e + F/2 (Eq. 12)
     const T ux = (m.jx + T(0.5) * Fx) * irho;
     const T uy = (m.jy + T(0.5) * Fy) * irho;
@@ -191,9 +231,9 @@ __device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T F
         // Eq. 49 / App. D: Cramer's rule on the 3x3 system
         const T num = -Csz * Cby * Rs1 - Csy * (Cbz * Rs2 - Csz * Rb);
         const T den = -Csx * Csz * Cby - Csy * (Csx * Cbz - Csz * Cbx);
-        const T dxux = num / den;
-        const T dyuy = (Rs1 - Csx * dxux) / Csy;
-        const T dzuz = (Rs2 - Csx * dxux) / Csz;
+        const T dxux = div_(num, den);
+        const T dyuy = div_(Rs1 - Csx * dxux, Csy);
+        const T dzuz = div_(Rs2 - Csx * dxux, Csz);
         // theta coefficients (Eq. 38-40 in the shear/bulk notation of App. D)
         const T qx = -rho * (T(3) * ux2 + P.an[0]);
         const T qy = -rho * (T(3) * uy2 + P.an[1]);
@@ -215,64 +255,110 @@ __device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T F
     const T t2d1 = k2d1 + wn * (E2d1 - k2d1);
     const T t2d2 = k2d2 + wn * (E2d2 - k2d2);
     const T onemw = T(1) - wn;
-    const T t110 = onemw * k110, t101 = onemw * k101, t011 = onemw * k011;
+    PostState<T> o;
+    o.dr = dr;
+    o.ux = ux;
+    o.uy = uy;
+    o.uz = uz;
+    o.t110 = onemw * k110;
+    o.t101 = onemw * k101;
+    o.t011 = onemw * k011;
     // B^-1 (end of App. D), deviations of k~_200, k~_020, k~_002 from cs2 rho
     const T third = T(1) / T(3);
-    const T d200 = (t2s + t2d1 + t2d2) * third;
-    const T d020 = (t2s - T(2) * t2d1 + t2d2) * third;
-    const T d002 = (t2s + t2d1 - T(2) * t2d2) * third;
-    const T hFx = T(0.5) * Fx, hFy = T(0.5) * Fy, hFz = T(0.5) * Fz;
+    o.d200 = (t2s + t2d1 + t2d2) * third;
+    o.d020 = (t2s - T(2) * t2d1 + t2d2) * third;
+    o.d002 = (t2s + t2d1 - T(2) * t2d2) * third;
+    o.hFx = T(0.5) * Fx;
+    o.hFy = T(0.5) * Fy;
+    o.hFz = T(0.5) * Fz;
+    return o;
+}
 
-    // back to populations: f~ = f^eq(rho,u) + M(u)^-1 (k~ - k^eq)  (Apps. E-G)
-    const AxisCols<T> X = axis_cols(ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0], cs2);
-    const AxisCols<T> Y = axis_cols(uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1], cs2);
-    const AxisCols<T> Z = axis_cols(uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2], cs2);
+// Back to populations: h~ = f^eq(rho, u) - w + M(u)^-1 (k~ - k^eq) (Apps. E-G).
+template <class V, class T>
+__device__ __forceinline__ void back_transform(V (&h)[Q], const PostState<V> &o, const Phys<T> &P)
+{
+    const AxisCols<V> X = axis_cols(o.ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0]);
+    const AxisCols<V> Y = axis_cols(o.uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]);
+    const AxisCols<V> Z = axis_cols(o.uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2]);
 
     // z stage of M^-1 on the sparse non-equilibrium central moments
-    T A00[3], A10[3], A01[3], A11[3], A20[3], A02[3];
+    V A00[3], A10[3], A01[3], A11[3], A20[3], A02[3];
 #pragma unroll
     for (int z = 0; z < 3; ++z) {
-        A00[z] = hFz * Z.g1[z] + d002 * Z.g2[z];
-        A10[z] = hFx * Z.g0[z] + t101 * Z.g1[z];
-        A01[z] = hFy * Z.g0[z] + t011 * Z.g1[z];
-        A11[z] = t110 * Z.g0[z];
-        A20[z] = d200 * Z.g0[z];
-        A02[z] = d020 * Z.g0[z];
+        A00[z] = fma_(o.hFz, Z.g1[z], o.d002 * Z.g2[z]);
+        A10[z] = fma_(o.hFx, Z.g0[z], o.t101 * Z.g1[z]);
+        A01[z] = fma_(o.hFy, Z.g0[z], o.t011 * Z.g1[z]);
+        A11[z] = o.t110 * Z.g0[z];
+        A20[z] = o.d200 * Z.g0[z];
+        A02[z] = o.d020 * Z.g0[z];
     }
-    // equilibrium factors: P_yz = phi_y phi_z, D_yz = phi_y phi_z - w_y w_z
+    // rho phi_x phi_y phi_z - w_x w_y w_z = (dr phi_x + dphi_x) P_yz + w_x D_yz with
+    // P_yz = phi_y phi_z and D_yz = phi_y phi_z - w_y w_z = dphi_y phi_z + w_y dphi_z
+    V ax[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) ax[x] = fma_(o.dr, X.phi[x], X.dphi[x]);
 #pragma unroll
     for (int y = 0; y < 3; ++y)
 #pragma unroll
         for (int z = 0; z < 3; ++z) {
-            const T B0 = A00[z] * Y.g0[y] + A01[z] * Y.g1[y] + A02[z] * Y.g2[y];
-            const T B1 = A10[z] * Y.g0[y] + A11[z] * Y.g1[y];
-            const T B2 = A20[z] * Y.g0[y];
-            const T Pyz = Y.phi[y] * Z.phi[z];
-            const T Dyz = Y.dphi[y] * Z.phi[z] + Y.w[y] * Z.dphi[z];
+            const V B0 = fma_(A00[z], Y.g0[y], fma_(A01[z], Y.g1[y], A02[z] * Y.g2[y]));
+            const V B1 = fma_(A10[z], Y.g0[y], A11[z] * Y.g1[y]);
+            const V B2 = A20[z] * Y.g0[y];
+            const V Pyz = Y.phi[y] * Z.phi[z];
+            const V Dyz = fma_(Y.dphi[y], Z.phi[z], Y.w[y] * Z.dphi[z]);
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
-                // rho phi_x phi_y phi_z - w_x w_y w_z = (dr phi_x + dphi_x) P_yz + w_x D_yz
-                const T ax = dr * X.phi[x] + X.dphi[x];
-                const T heq = ax * Pyz + X.w[x] * Dyz;
-                const T hne = B0 * X.g0[x] + B1 * X.g1[x] + B2 * X.g2[x];
-                h[dir_of(x - 1, y - 1, z - 1)] = heq + hne;
+                const V heq = fma_(ax[x], Pyz, X.w[x] * Dyz);
+                h[dir_of(x - 1, y - 1, z - 1)] = fma_(B0, X.g0[x], fma_(B1, X.g1[x], fma_(B2, X.g2[x], heq)));
             }
         }
+}
+
+// One collision, in place on the deviations h of one node (Sec. 3.2 steps, App. D).
+template <class T, int CORR>
+__device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T Fx, T Fy, T Fz,
+                                                T grx = T(0), T gry = T(0), T grz = T(0))
+{
+    const RawMoments<T> m = raw_moments(h, P);
+    const PostState<T> o = relax_node<T, CORR>(m, P, Fx, Fy, Fz, grx, gry, grz);
+    back_transform(h, o, P);
     NodeMacro<T> out;
-    out.rho = rho;
-    out.ux = ux;
-    out.uy = uy;
-    out.uz = uz;
+    out.rho = T(1) + o.dr;
+    out.ux = o.ux;
+    out.uy = o.uy;
+    out.uz = o.uz;
     return out;
+}
+
+// Two collisions (two nodes in the lanes of F2), in place.  The linear transforms
+// run in packed FP32x2 instructions; the per-node relaxation runs per lane.
+template <int CORR>
+__device__ __forceinline__ void collide_pair(F2 (&h)[Q], const Phys<float> &P, F2 F0, F2 F1, F2 F2_)
+{
+    const RawMoments<F2> m = raw_moments(h, P);
+    RawMoments<float> a, b;
+#define LBC_SPLIT(f) a.f = m.f.v.x; b.f = m.f.v.y;
+    LBC_SPLIT(dr) LBC_SPLIT(jx) LBC_SPLIT(jy) LBC_SPLIT(jz) LBC_SPLIT(pxx) LBC_SPLIT(pyy) LBC_SPLIT(pzz)
+    LBC_SPLIT(pxy) LBC_SPLIT(pxz) LBC_SPLIT(pyz)
+#undef LBC_SPLIT
+    const PostState<float> oa = relax_node<float, CORR>(a, P, F0.v.x, F1.v.x, F2_.v.x, 0.f, 0.f, 0.f);
+    const PostState<float> ob = relax_node<float, CORR>(b, P, F0.v.y, F1.v.y, F2_.v.y, 0.f, 0.f, 0.f);
+    PostState<F2> o;
+#define LBC_JOIN(f) o.f = F2(oa.f, ob.f);
+    LBC_JOIN(dr) LBC_JOIN(ux) LBC_JOIN(uy) LBC_JOIN(uz) LBC_JOIN(hFx) LBC_JOIN(hFy) LBC_JOIN(hFz)
+    LBC_JOIN(t110) LBC_JOIN(t101) LBC_JOIN(t011) LBC_JOIN(d200) LBC_JOIN(d020) LBC_JOIN(d002)
+#undef LBC_JOIN
+    back_transform(h, o, P);
 }
 
 // Equilibrium deviations h^eq_a = f^eq_a(rho, u) - w_a (init and moving walls).
 template <class T>
 __device__ __forceinline__ void equilibrium_dev(T (&h)[Q], const Phys<T> &P, T rho, T ux, T uy, T uz)
 {
-    const AxisCols<T> X = axis_cols(ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0], P.cs2);
-    const AxisCols<T> Y = axis_cols(uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1], P.cs2);
-    const AxisCols<T> Z = axis_cols(uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2], P.cs2);
+    const AxisCols<T> X = axis_cols(ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0]);
+    const AxisCols<T> Y = axis_cols(uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]);
+    const AxisCols<T> Z = axis_cols(uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2]);
     const T dr = rho - T(1);
 #pragma unroll
     for (int y = 0; y < 3; ++y)

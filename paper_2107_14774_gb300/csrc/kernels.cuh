@@ -121,8 +121,8 @@ __device__ __forceinline__ void pull_node(typename Codec<ST>::T (&h)[Q], const t
         for (int a = 0; a < Q; ++a) rho_w += C::load(__ldg(src + (long long)a * N + q.base), D.w[a], D.iscale[a]);
         // f^eq(rho_w, (U,0,0)): only the x factor depends on U; the correction
         // f^eq_a - f^eq_opp(a) = rho_w phi_y phi_z (phi_x(ex) - phi_x(-ex)) = rho_w phi_y phi_z ex U
-        const AxisCols<T> Y = axis_cols(T(0), P.ic[1], P.ic2[1], P.w0[1], P.wpm[1], P.cs2);
-        const AxisCols<T> Z = axis_cols(T(0), P.ic[2], P.ic2[2], P.w0[2], P.wpm[2], P.cs2);
+        const AxisCols<T> Y = axis_cols(T(0), P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]);
+        const AxisCols<T> Z = axis_cols(T(0), P.ic[2], P.ic2[2], P.w0[2], P.wpm[2]);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             if (ey(a) == -1 && ex(a) != 0) {
@@ -197,6 +197,126 @@ k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__r
     collide<T, CORR>(h, P, Fx, Fy, Fz, grx, gry, grz);
 #pragma unroll
     for (int a = 0; a < Q; ++a) dst[(long long)a * N + q.base] = C::store(h[a], D.w[a], D.scale[a]);
+}
+
+// ---------------------------------------------------------------------------
+// Two-node variant of k_step for the FP32-arithmetic storage forms.  Each thread
+// updates the x-adjacent nodes (i0, i0+1), i0 even: populations with ex = 0 and
+// every store move as one aligned 2-element vector; the two x-shifted source
+// elements of ex = +-1 are single loads.  The linear parts of the collision run
+// in packed FP32x2 instructions (collide_pair).  Offsets are 32-bit (the host
+// only selects this kernel when 27 N < 2^32), the source row of each (ey, ez) is
+// computed once, and periodic wrap in y and z is folded into those row offsets.
+// Requirements (checked on the host): nx even, no walls normal to x, no moving
+// lid, corrections other than FULL.
+
+template <int ST> struct PairIO;
+template <> struct PairIO<LB_F32> {
+    using S = float;
+    static __device__ __forceinline__ F2 load2(const S *p, float w, float)
+    {
+        return F2(__ldg(reinterpret_cast<const float2 *>(p))) - F2(w);
+    }
+    static __device__ __forceinline__ void store2(S *p, F2 h, float w, float)
+    {
+        *reinterpret_cast<float2 *>(p) = (h + F2(w)).v;
+    }
+};
+template <> struct PairIO<LB_F32_SHIFTED> {
+    using S = float;
+    static __device__ __forceinline__ F2 load2(const S *p, float, float)
+    {
+        return F2(__ldg(reinterpret_cast<const float2 *>(p)));
+    }
+    static __device__ __forceinline__ void store2(S *p, F2 h, float, float) { *reinterpret_cast<float2 *>(p) = h.v; }
+};
+template <> struct PairIO<LB_F16_SHIFTED> {
+    using S = __half;
+    static __device__ __forceinline__ F2 load2(const S *p, float, float iscale)
+    {
+        return F2(__half22float2(__ldg(reinterpret_cast<const __half2 *>(p)))) * F2(iscale);
+    }
+    static __device__ __forceinline__ void store2(S *p, F2 h, float, float scale)
+    {
+        *reinterpret_cast<__half2 *>(p) = __float22half2_rn((h * F2(scale)).v);
+    }
+};
+template <> struct PairIO<LB_BF16_SHIFTED> {
+    using S = __nv_bfloat16;
+    static __device__ __forceinline__ F2 load2(const S *p, float, float)
+    {
+        return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p))));
+    }
+    static __device__ __forceinline__ void store2(S *p, F2 h, float, float)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(h.v);
+    }
+};
+
+// Base pointers of the 27 direction arrays of the source and destination
+// buffers, passed by value so that every load and store address is one
+// multiply-add of a 32-bit element index onto a kernel-parameter pointer.
+template <class S>
+struct DirPtrs {
+    const S *src[Q];
+    S *dst[Q];
+};
+
+template <int ST, int CORR>
+__global__ void __launch_bounds__(kBlockThreads)
+k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
+            float F2s, const float *__restrict__ ff)
+{
+    using C = Codec<ST>;
+    using IO = PairIO<ST>;
+    const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i0 >= g.nx || j >= g.ny) return;
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    int ys[3], zs[3];
+    bool yo[3], zo[3];
+    axis_sources(j, g.ny, g.wall[1], ys, yo);
+    axis_sources(k, g.nz, g.wall[2], zs, zo);
+    unsigned rowbase[3][3];
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) rowbase[cy][cz] = (unsigned)zs[cz] * nxy + (unsigned)ys[cy] * nx;
+    const unsigned self = rowbase[1][1] + (unsigned)i0;
+    const unsigned xm = (i0 == 0) ? nx - 1u : (unsigned)i0 - 1u;       // source of ex = +1 for node i0
+    const unsigned xp = (i0 + 2 == g.nx) ? 0u : (unsigned)i0 + 2u;     // source of ex = -1 for node i0+1
+    F2 h[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
+        if (yo[cy] | zo[cz]) {
+            // half-way bounce-back across a y or z wall: f_a(x) = S_opp(a)(x) for both nodes
+            h[a] = IO::load2(ptr.src[opp(a)] + self, D.w[a], D.iscale[a]);
+        } else {
+            const unsigned rb = rowbase[cy][cz];
+            const typename C::S *p = ptr.src[a];
+            if (cx == 1) {
+                h[a] = IO::load2(p + (rb + (unsigned)i0), D.w[a], D.iscale[a]);
+            } else if (cx == 2) {  // ex = +1: sources i0 - 1, i0
+                h[a] = F2(C::load(__ldg(p + (rb + xm)), D.w[a], D.iscale[a]),
+                          C::load(__ldg(p + (rb + (unsigned)i0)), D.w[a], D.iscale[a]));
+            } else {               // ex = -1: sources i0 + 1, i0 + 2
+                h[a] = F2(C::load(__ldg(p + (rb + (unsigned)i0 + 1u)), D.w[a], D.iscale[a]),
+                          C::load(__ldg(p + (rb + xp)), D.w[a], D.iscale[a]));
+            }
+        }
+    }
+    F2 Fx(F0), Fy(F1), Fz(F2s);
+    if (ff) {
+        const unsigned N = (unsigned)g.N;
+        Fx += F2(__ldg(reinterpret_cast<const float2 *>(ff + self)));
+        Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
+        Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
+    }
+    collide_pair<CORR>(h, P, Fx, Fy, Fz);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) IO::store2(ptr.dst[a] + self, h[a], D.w[a], D.scale[a]);
 }
 
 // Density of every node (pre-pass of LB_CORR_FULL).

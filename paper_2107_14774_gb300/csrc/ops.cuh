@@ -21,6 +21,7 @@ struct LaunchArgs {
     cudaStream_t stream;
     const void *force_field;  // device, compute type, [3][N] or null
     void *rho_field;          // device, compute type, [N] (FULL) or null
+    bool pair_disabled;       // force the one-node kernel (tests compare both)
 };
 
 inline void launch_shape(const Geom &g, dim3 &grid, dim3 &block)
@@ -51,6 +52,8 @@ struct Ops {
     static Phys<T> phys(const LaunchArgs &a) { return make_phys<T>(a.r, a.s, a.cs2, a.wn, a.wb); }
 
     static cudaError_t step(const LaunchArgs &a, const void *src, void *dst);
+    static bool use_pair(const LaunchArgs &a);
+    static cudaError_t step_pair(const LaunchArgs &a, const void *src, void *dst);
     static cudaError_t gather(const LaunchArgs &a, const void *src, void *rho, void *u, void *f);
     static cudaError_t scatter(const LaunchArgs &a, void *dst, const void *rho, const void *u, const void *f);
     static cudaError_t reduce_partial(const LaunchArgs &a, const void *src, double *partial, int nblocks,
@@ -71,6 +74,7 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
     if (a.corr == LB_CORR_FULL) {
         k_density<ST><<<grid, block, 0, a.stream>>>(s, a.g, P, D, (T)a.lid_u, rf);
     }
+    if (use_pair(a)) return step_pair(a, src, dst);
     switch (a.corr) {
     case LB_CORR_NONE:
         k_step<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
@@ -90,6 +94,52 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
         break;
     }
     return cudaGetLastError();
+}
+
+// The two-node kernel covers the FP32-arithmetic storage forms on lattices with an
+// even nx, no walls normal to x, no moving lid, no FULL corrections and 32-bit
+// offsets; everything else takes the one-node kernel.
+template <int ST>
+bool Ops<ST>::use_pair(const LaunchArgs &a)
+{
+    if (ST == LB_F64 || a.pair_disabled) return false;
+    return (a.g.nx % 2 == 0) && !a.g.wall[0] && a.lid_u == 0.0 && a.corr != LB_CORR_FULL &&
+           (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
+}
+
+template <int ST>
+cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
+{
+    if constexpr (ST == LB_F64) {
+        return cudaErrorInvalidValue;
+    } else {
+        const int np = a.g.nx / 2;
+        int bx = kBlockX;
+        while (bx > 1 && bx / 2 >= np) bx /= 2;
+        const int by = kBlockThreads / bx;
+        const dim3 block(bx, by, 1), grid((np + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
+        const Phys<float> P = phys(a);
+        const DirConst<float> D = dirs(a);
+        DirPtrs<S> ptr;
+        for (int q = 0; q < Q; ++q) {
+            ptr.src[q] = static_cast<const S *>(src) + (size_t)q * (size_t)a.g.N;
+            ptr.dst[q] = static_cast<S *>(dst) + (size_t)q * (size_t)a.g.N;
+        }
+        const float *ff = static_cast<const float *>(a.force_field);
+        const float F0 = (float)a.F[0], F1 = (float)a.F[1], F2 = (float)a.F[2];
+        switch (a.corr) {
+        case LB_CORR_NONE:
+            k_step_pair<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            break;
+        case LB_CORR_LOWMACH:
+            k_step_pair<ST, LB_CORR_LOWMACH><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            break;
+        default:
+            k_step_pair<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            break;
+        }
+        return cudaGetLastError();
+    }
 }
 
 template <int ST>

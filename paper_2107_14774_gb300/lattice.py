@@ -36,10 +36,12 @@ class Lattice:
     storage: "f64", "f32", "f32s" (shifted FP32), "f16s", "bf16s" (shifted FP16 /
     BF16, FP32 arithmetic).  corr: "none", "lowmach", "local", "full".
     walls: any of "x", "y", "z" (half-way bounce-back walls normal to that axis).
+    kernel: "auto" (two nodes per thread where possible) or "one" (one node per thread).
     """
 
     def __init__(self, nx, ny, nz, r_y=1.0, r_z=1.0, nu=0.01, zeta=0.0, cs2=0.0, storage="f32",
-                 corr="local", walls="", force=(0.0, 0.0, 0.0), lid_u=0.0, stream=None, device=None):
+                 corr="local", walls="", force=(0.0, 0.0, 0.0), lid_u=0.0, stream=None, device=None,
+                 kernel="auto"):
         self.lib = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
@@ -53,6 +55,7 @@ class Lattice:
         cfg.force = (ctypes.c_double * 3)(*force)
         cfg.lid_u = lid_u
         cfg.stream = s.cuda_stream
+        cfg.kernel = {"auto": 0, "one": 1}[kernel]
         self.cfg = cfg
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
