@@ -164,6 +164,33 @@ lb_status lb_set_state(lb_ctx *ctx, const void *src, long long time_step);
 /* Number of completed time steps since the last lb_init / lb_set_populations. */
 long long lb_time_step(const lb_ctx *ctx);
 
+/* Set the relaxation rates directly, 0 < omega < 2 (instead of nu, zeta). */
+lb_status lb_set_rates(lb_ctx *ctx, double omega_nu, double omega_xi);
+
+/* Mean kinetic energy J = (1/N) sum_x rho |u|^2 / 2 of the current populations,
+ * u including the F/2 shift (Eq. 12); FP64 sum, deterministic.  Synchronises. */
+lb_status lb_objective_ke(lb_ctx *ctx, double *J);
+
+/* Discrete adjoint of T fused steps (Sec. 3.2 update, transposed) for the mean
+ * kinetic energy J after T steps, starting from the current state.  Returns J,
+ * dJ/dF [3][N] (real; the gradient with respect to the per-node body force field,
+ * i.e. to the total force at each node) and dJ/domega = (dJ/domega_nu,
+ * dJ/domega_xi) on the host.  The forward states are kept every K steps
+ * (checkpoints) and each K-step segment is recomputed once during the backward
+ * sweep, so device memory grows as (ceil(T/K) + K) stored states; the temporary
+ * buffers are allocated and freed inside the call.  On return the context holds
+ * the state after the T steps (as after lb_step(ctx, T)).  Corrections NONE,
+ * LOWMACH or LOCAL; no moving lid (LB_EINVAL otherwise).  Synchronises. */
+lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2], double *J);
+
+/* Vector-Jacobian product of the per-node collision alone, for n independent
+ * nodes (device pointers, real type): f [27][n] pre-collision populations,
+ * F [3][n] body force, lam [27][n] = dJ/d(post-collision populations).  Writes
+ * f_bar [27][n] = dJ/df, F_bar [3][n] = dJ/dF and w_bar = (dJ/domega_nu,
+ * dJ/domega_xi) summed over the nodes (host).  Synchronises. */
+lb_status lb_collide_vjp(lb_ctx *ctx, long long n, const void *f, const void *F, const void *lam, void *f_bar,
+                         void *F_bar, double w_bar[2]);
+
 /* Message of the last error on this thread ("" if none). */
 const char *lb_last_error(void);
 

@@ -10,3 +10,4 @@ from ._lib import (  # noqa: F401
     LB_F32_SHIFTED, LB_F64, LB_WALL_X, LB_WALL_Y, LB_WALL_Z, LBError, lb_config,
 )
 from .lattice import Lattice, STORAGE, CORR  # noqa: F401
+from .autograd import KineticEnergyRollout, kinetic_energy_rollout  # noqa: F401

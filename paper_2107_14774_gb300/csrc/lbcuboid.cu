@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "lbcuboid.h"
 #include "ops.cuh"
@@ -418,6 +420,157 @@ lb_status lb_set_state(lb_ctx *c, const void *src, long long time_step)
     c->t = time_step;
     c->fresh = false;
     return LB_OK;
+}
+
+lb_status lb_set_rates(lb_ctx *c, double omega_nu, double omega_xi)
+{
+    if (!c) return fail(LB_EINVAL, "lb_set_rates: null context");
+    if (!(omega_nu > 0.0 && omega_nu < 2.0) || !(omega_xi > 0.0 && omega_xi < 2.0))
+        return fail(LB_EINVAL, "lb_set_rates: relaxation rates must lie in (0, 2)");
+    c->wn = omega_nu;
+    c->wb = omega_xi;
+    return LB_OK;
+}
+
+namespace {
+
+// Device scratch owned by one adjoint / objective call (freed on every exit path).
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    cudaError_t alloc(void **p, size_t bytes)
+    {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+
+lb_status sum_pairs(lb_ctx *c, const double *dev, long long nblocks, double out[2])
+{
+    std::vector<double> h(2 * (size_t)nblocks);
+    LB_CUDA(cudaMemcpyAsync(h.data(), dev, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    out[0] = out[1] = 0.0;
+    for (long long b = 0; b < nblocks; ++b) {
+        out[0] += h[2 * b];
+        out[1] += h[2 * b + 1];
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+lb_status lb_objective_ke(lb_ctx *c, double *J)
+{
+    if (!c || !J) return fail(LB_EINVAL, "lb_objective_ke: null argument");
+    Scratch s;
+    const long long nb = adjoint_blocks(c->g);
+    double *jpart = nullptr;
+    LB_CUDA(s.alloc((void **)&jpart, 2 * nb * sizeof(double)));
+    LB_CUDA(cudaMemsetAsync(jpart, 0, 2 * nb * sizeof(double), c->stream));
+    const LaunchArgs a = launch_args(c);
+    const void *src = c->buf[c->cur];
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) {
+        return decltype(ops)::adjoint_seed(a, src, nullptr, nullptr, jpart);
+    }));
+    double out[2];
+    lb_status st = sum_pairs(c, jpart, nb, out);
+    if (st) return st;
+    *J = out[0];
+    return LB_OK;
+}
+
+lb_status lb_adjoint_ke(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2], double *J)
+{
+    if (!c || !dJdF || !dJdomega) return fail(LB_EINVAL, "lb_adjoint_ke: null argument");
+    if (T < 1 || K < 1) return fail(LB_EINVAL, "lb_adjoint_ke: T and K must be >= 1");
+    if (c->cfg.corr == LB_CORR_FULL) return fail(LB_EINVAL, "lb_adjoint_ke: corrections FULL are not supported");
+    if (c->cfg.lid_u != 0.0) return fail(LB_EINVAL, "lb_adjoint_ke: a moving lid is not supported");
+    if (K > T) K = T;
+    const size_t sb = lb_state_bytes(c);
+    const long long N = c->g.N;
+    const int nck = (T + K - 1) / K;
+    const long long nb = adjoint_blocks(c->g);
+    Scratch s;
+    char *ck = nullptr, *seg = nullptr;
+    void *lam[2] = {nullptr, nullptr}, *dF = nullptr;
+    double *jpart = nullptr, *wpart = nullptr;
+    LB_CUDA(s.alloc((void **)&ck, (size_t)nck * sb));
+    LB_CUDA(s.alloc((void **)&seg, (size_t)K * sb));
+    LB_CUDA(s.alloc(&lam[0], (size_t)Q * N * c->rbytes));
+    LB_CUDA(s.alloc(&lam[1], (size_t)Q * N * c->rbytes));
+    LB_CUDA(s.alloc(&dF, 3 * (size_t)N * c->rbytes));
+    LB_CUDA(s.alloc((void **)&jpart, 2 * nb * sizeof(double)));
+    LB_CUDA(s.alloc((void **)&wpart, 2 * nb * sizeof(double)));
+    LB_CUDA(cudaMemsetAsync(jpart, 0, 2 * nb * sizeof(double), c->stream));
+    LB_CUDA(cudaMemsetAsync(wpart, 0, 2 * nb * sizeof(double), c->stream));
+    const int storage = c->cfg.storage;
+
+    // forward sweep with a checkpoint every K steps
+    for (int n = 0; n < T; ++n) {
+        if (n % K == 0)
+            LB_CUDA(cudaMemcpyAsync(ck + (size_t)(n / K) * sb, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        lb_status st = lb_step(c, 1);
+        if (st) return st;
+    }
+    const LaunchArgs a = launch_args(c);
+    {
+        const void *src = c->buf[c->cur];
+        LB_CUDA(dispatch(storage, [&](auto ops) { return decltype(ops)::adjoint_seed(a, src, lam[0], dF, jpart); }));
+    }
+    // backward sweep: recompute each segment from its checkpoint, then walk it back
+    int li = 0;
+    for (int sgm = nck - 1; sgm >= 0; --sgm) {
+        const int n0 = sgm * K, n1 = std::min(T, n0 + K);
+        LB_CUDA(cudaMemcpyAsync(seg, ck + (size_t)sgm * sb, sb, cudaMemcpyDeviceToDevice, c->stream));
+        for (int i = 1; i < n1 - n0; ++i) {
+            const void *src = seg + (size_t)(i - 1) * sb;
+            void *dst = seg + (size_t)i * sb;
+            LB_CUDA(dispatch(storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); }));
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            const void *src = seg + (size_t)(n - n0) * sb;
+            const void *lin = lam[li];
+            void *lout = lam[li ^ 1];
+            LB_CUDA(dispatch(storage, [&](auto ops) {
+                return decltype(ops)::adjoint_step(a, src, lin, lout, dF, wpart);
+            }));
+            li ^= 1;
+        }
+    }
+    LB_CUDA(cudaMemcpyAsync(dJdF, dF, 3 * (size_t)N * c->rbytes, cudaMemcpyDefault, c->stream));
+    double jj[2];
+    lb_status st = sum_pairs(c, jpart, nb, jj);
+    if (st) return st;
+    st = sum_pairs(c, wpart, nb, dJdomega);
+    if (st) return st;
+    if (J) *J = jj[0];
+    return LB_OK;
+}
+
+lb_status lb_collide_vjp(lb_ctx *c, long long n, const void *f, const void *F, const void *lam, void *f_bar,
+                         void *F_bar, double w_bar[2])
+{
+    if (!c || !f || !F || !lam || !f_bar || !F_bar || !w_bar || n < 1)
+        return fail(LB_EINVAL, "lb_collide_vjp: bad argument");
+    if (c->cfg.corr == LB_CORR_FULL) return fail(LB_EINVAL, "lb_collide_vjp: corrections FULL are not supported");
+    for (const void *p : {f, F, lam, (const void *)f_bar, (const void *)F_bar})
+        if (!is_device_pointer(p)) return fail(LB_EINVAL, "lb_collide_vjp: device pointers required");
+    Scratch s;
+    const long long nb = (n + kAdjThreads - 1) / kAdjThreads;
+    double *wpart = nullptr;
+    LB_CUDA(s.alloc((void **)&wpart, 2 * nb * sizeof(double)));
+    LB_CUDA(cudaMemsetAsync(wpart, 0, 2 * nb * sizeof(double), c->stream));
+    const LaunchArgs a = launch_args(c);
+    LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) {
+        return decltype(ops)::collide_vjp(a, f, F, lam, f_bar, F_bar, n, wpart);
+    }));
+    return sum_pairs(c, wpart, nb, w_bar);
 }
 
 const char *lb_last_error(void) { return g_last_error.c_str(); }

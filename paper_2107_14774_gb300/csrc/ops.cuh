@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "adjoint.cuh"
 
 namespace lbc {
 
@@ -58,7 +59,21 @@ struct Ops {
     static cudaError_t scatter(const LaunchArgs &a, void *dst, const void *rho, const void *u, const void *f);
     static cudaError_t reduce_partial(const LaunchArgs &a, const void *src, double *partial, int nblocks,
                                       unsigned *status);
+    // adjoint (mean kinetic energy objective); the grid of these launches is
+    // launch_shape(a.g), and jpart / wpart hold two doubles per block of it
+    static cudaError_t adjoint_seed(const LaunchArgs &a, const void *src, void *lam, void *dJdF, double *jpart);
+    static cudaError_t adjoint_step(const LaunchArgs &a, const void *src, const void *lam_in, void *lam_out,
+                                    void *dJdF, double *wpart);
+    static cudaError_t collide_vjp(const LaunchArgs &a, const void *f, const void *F, const void *L, void *fb,
+                                   void *Fb, long long n, double *wpart);
 };
+
+inline long long adjoint_blocks(const Geom &g)
+{
+    dim3 grid, block;
+    launch_shape(g, grid, block);
+    return (long long)grid.x * grid.y * grid.z;
+}
 
 template <int ST>
 cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
@@ -172,6 +187,75 @@ cudaError_t Ops<ST>::reduce_partial(const LaunchArgs &a, const void *src, double
     k_reduce_partial<ST><<<nblocks, kReduceThreads, 0, a.stream>>>(
         static_cast<const S *>(src), a.g, phys(a), dirs(a), (T)a.F[0], (T)a.F[1], (T)a.F[2],
         static_cast<const T *>(a.force_field), (T)a.lid_u, partial, status);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Ops<ST>::adjoint_seed(const LaunchArgs &a, const void *src, void *lam, void *dJdF, double *jpart)
+{
+    dim3 grid, block;
+    launch_shape(a.g, grid, block);
+    k_adjoint_seed<ST><<<grid, block, 0, a.stream>>>(static_cast<const S *>(src), a.g, phys(a), dirs(a), (T)a.F[0],
+                                                     (T)a.F[1], (T)a.F[2], static_cast<const T *>(a.force_field),
+                                                     static_cast<T *>(lam), static_cast<T *>(dJdF), jpart);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Ops<ST>::adjoint_step(const LaunchArgs &a, const void *src, const void *lam_in, void *lam_out,
+                                  void *dJdF, double *wpart)
+{
+    dim3 grid, block;
+    launch_shape(a.g, grid, block);
+    const S *s = static_cast<const S *>(src);
+    const T *li = static_cast<const T *>(lam_in);
+    T *lo = static_cast<T *>(lam_out);
+    const T *ff = static_cast<const T *>(a.force_field);
+    T *dF = static_cast<T *>(dJdF);
+    const Phys<T> P = phys(a);
+    const DirConst<T> D = dirs(a);
+    switch (a.corr) {
+    case LB_CORR_NONE:
+        k_adjoint<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(s, li, lo, a.g, P, D, (T)a.F[0], (T)a.F[1],
+                                                                   (T)a.F[2], ff, dF, wpart);
+        break;
+    case LB_CORR_LOWMACH:
+        k_adjoint<ST, LB_CORR_LOWMACH><<<grid, block, 0, a.stream>>>(s, li, lo, a.g, P, D, (T)a.F[0], (T)a.F[1],
+                                                                      (T)a.F[2], ff, dF, wpart);
+        break;
+    case LB_CORR_LOCAL:
+        k_adjoint<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(s, li, lo, a.g, P, D, (T)a.F[0], (T)a.F[1],
+                                                                    (T)a.F[2], ff, dF, wpart);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Ops<ST>::collide_vjp(const LaunchArgs &a, const void *f, const void *F, const void *L, void *fb,
+                                 void *Fb, long long n, double *wpart)
+{
+    const int blocks = (int)((n + kAdjThreads - 1) / kAdjThreads);
+    const T *pf = static_cast<const T *>(f), *pF = static_cast<const T *>(F), *pL = static_cast<const T *>(L);
+    T *pfb = static_cast<T *>(fb), *pFb = static_cast<T *>(Fb);
+    const Phys<T> P = phys(a);
+    const DirConst<T> D = dirs(a);
+    switch (a.corr) {
+    case LB_CORR_NONE:
+        k_collide_vjp<ST, LB_CORR_NONE><<<blocks, kAdjThreads, 0, a.stream>>>(pf, pF, pL, pfb, pFb, n, P, D, wpart);
+        break;
+    case LB_CORR_LOWMACH:
+        k_collide_vjp<ST, LB_CORR_LOWMACH><<<blocks, kAdjThreads, 0, a.stream>>>(pf, pF, pL, pfb, pFb, n, P, D,
+                                                                                 wpart);
+        break;
+    case LB_CORR_LOCAL:
+        k_collide_vjp<ST, LB_CORR_LOCAL><<<blocks, kAdjThreads, 0, a.stream>>>(pf, pF, pL, pfb, pFb, n, P, D, wpart);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

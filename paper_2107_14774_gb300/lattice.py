@@ -167,3 +167,35 @@ class Lattice:
     def set_state(self, state, time_step: int = 0):
         check(self.lib.lb_set_state(self.ctx, _ptr(state), int(time_step)))
         return self
+
+    # ------------------------------------------------------------ adjoint
+    def set_rates(self, omega_nu: float, omega_xi: float):
+        """lb_set_rates: relaxation rates directly (0 < omega < 2)."""
+        check(self.lib.lb_set_rates(self.ctx, float(omega_nu), float(omega_xi)))
+        return self
+
+    def objective_ke(self) -> float:
+        """lb_objective_ke: mean kinetic energy of the current state (FP64 sum)."""
+        out = ctypes.c_double()
+        check(self.lib.lb_objective_ke(self.ctx, ctypes.byref(out)))
+        return out.value
+
+    def adjoint_ke(self, T: int, K: int, dJdF=None):
+        """lb_adjoint_ke: run T steps and the discrete adjoint of the mean kinetic
+        energy; returns (J, dJ/dF [3,nz,ny,nx], (dJ/domega_nu, dJ/domega_xi))."""
+        if dJdF is None:
+            dJdF = torch.empty((3,) + self.shape, dtype=self.dtype, device=self.device)
+        dw = (ctypes.c_double * 2)()
+        J = ctypes.c_double()
+        check(self.lib.lb_adjoint_ke(self.ctx, int(T), int(K), _ptr(dJdF), dw, ctypes.byref(J)))
+        return J.value, dJdF, (dw[0], dw[1])
+
+    def collide_vjp(self, f, F, lam):
+        """lb_collide_vjp: per-node VJP of the collision for n nodes ([27,n], [3,n], [27,n])."""
+        n = f.shape[1]
+        f, F, lam = (x.to(self.device, self.dtype).contiguous() for x in (f, F, lam))
+        fb = torch.empty_like(f)
+        Fb = torch.empty_like(F)
+        wb = (ctypes.c_double * 2)()
+        check(self.lib.lb_collide_vjp(self.ctx, n, _ptr(f), _ptr(F), _ptr(lam), _ptr(fb), _ptr(Fb), wb))
+        return fb, Fb, (wb[0], wb[1])
