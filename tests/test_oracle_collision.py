@@ -170,3 +170,79 @@ def test_corrections_act_on_a_cuboid_lattice(oracle_mod):
     loc = oracle_mod.Oracle(corr=oracle_mod.CORR_LOCAL, **kw)
     f = synth.random_populations(1, seed=19)[0]
     assert np.abs(loc.collide_node(f) - none.collide_node(f)).max() > 1e-6
+
+
+def _ce_moments(cs2, r, s, wn, wb, rho, u, gr, d):
+    """Second-order non-equilibrium central moments predicted by the Chapman-Enskog
+    analysis of Sec. 2.4-2.5 for prescribed diagonal strain rates d = (dxux, dyuy,
+    dzuz), velocity u and density gradient gr: Eq. 33d-f with the error terms of
+    Eq. 22a-f and the corrections fixed by Eq. 37, n_j^eq(1) = -(1 - w_j/2)(E_js + E_jg).
+    Returns (n7, n8, n9, n7eq1, n8eq1, n9eq1)."""
+    ux, uy, uz = u
+    X, Y, Z = d
+    dx_rux = rho * X + ux * gr[0]       # d(rho u_x)/dx
+    dy_ruy = rho * Y + uy * gr[1]
+    dz_ruz = rho * Z + uz * gr[2]
+    a, b, c = 3 * cs2 - 1, 3 * cs2 - r * r, 3 * cs2 - s * s
+    E7 = (a * dx_rux - b * dy_ruy) / wn + 3 * rho / wn * (ux * ux * X - uy * uy * Y)
+    E8 = (a * dx_rux - c * dz_ruz) / wn + 3 * rho / wn * (ux * ux * X - uz * uz * Z)
+    E9 = (a * dx_rux + b * dy_ruy + c * dz_ruz) / wb + 3 * rho / wb * (ux * ux * X + uy * uy * Y + uz * uz * Z)
+    q7, q8, q9 = -(1 - wn / 2) * E7, -(1 - wn / 2) * E8, -(1 - wb / 2) * E9
+    n7 = -2 * cs2 * rho / wn * (X - Y) + E7 + q7
+    n8 = -2 * cs2 * rho / wn * (X - Z) + E8 + q8
+    n9 = -2 * cs2 * rho / wb * (X + Y + Z) + E9 + q9
+    return n7, n8, n9, q7, q8, q9
+
+
+@pytest.mark.parametrize("r,s,cs2", [(0.5, 2.0, 1 / 12), (1.0, 0.5, 0.1), (0.406, 1.3, 0.04)])
+def test_strain_rates_invert_the_chapman_enskog_moments(oracle_mod, r, s, cs2):
+    """The local strain-rate formulas (Eq. 44-49, App. D; FULL with density gradients)
+    recover the diagonal strain rates from the non-equilibrium moments that the
+    Chapman-Enskog analysis (Eq. 22, 33, 37) predicts for them."""
+    wn, wb = 1.45, 1.15
+    o = oracle_mod.Oracle(r=r, s=s, cs2=cs2, omega_nu=wn, omega_xi=wb, corr=oracle_mod.CORR_FULL)
+    ex = o.moment_exponents()
+    idx = {"%d%d%d" % tuple(ex[:, j]): j for j in range(27)}
+    rng = np.random.default_rng(7)
+    for _ in range(6):
+        rho = 1 + 0.02 * rng.standard_normal()
+        u = 0.06 * rng.standard_normal(3)
+        gr = 0.01 * rng.standard_normal(3)
+        d = 1e-3 * rng.standard_normal(3)
+        n7, n8, n9, *_ = _ce_moments(cs2, r, s, wn, wb, rho, u, gr, d)
+        # central moments with k200 - k020 = n7, k200 - k002 = n8, trace - 3 cs2 rho = n9
+        k = np.zeros(27)
+        k200 = cs2 * rho + (n9 + n7 + n8) / 3
+        k[idx["200"]], k[idx["020"]], k[idx["002"]] = k200, k200 - n7, k200 - n8
+        k[idx["000"]] = rho
+        np.testing.assert_allclose(o.strain_rates(k, rho, u, gr, aliasing=True), d, rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("r,s,cs2", [(0.5, 2.0, 1 / 12), (1.0, 0.5, 0.1)])
+def test_corrected_equilibria_cancel_the_truncation_errors(oracle_mod, r, s, cs2):
+    """With the recovered strain rates, the correction of the combined equilibria built
+    from the theta and lambda coefficients (Eq. 38-40; App. D) equals
+    -(1 - omega/2)(E_s + E_g) of Eq. 37 with the error terms of Eq. 22."""
+    wn, wb = 1.45, 1.15
+    o = oracle_mod.Oracle(r=r, s=s, cs2=cs2, omega_nu=wn, omega_xi=wb, corr=oracle_mod.CORR_FULL)
+    ex = o.moment_exponents()
+    idx = {"%d%d%d" % tuple(ex[:, j]): j for j in range(27)}
+    rng = np.random.default_rng(9)
+    for _ in range(6):
+        rho = 1 + 0.02 * rng.standard_normal()
+        u = 0.06 * rng.standard_normal(3)
+        gr = 0.01 * rng.standard_normal(3)
+        d = 1e-3 * rng.standard_normal(3)
+        n7, n8, n9, q7, q8, q9 = _ce_moments(cs2, r, s, wn, wb, rho, u, gr, d)
+        k = np.zeros(27)
+        k200 = cs2 * rho + (n9 + n7 + n8) / 3
+        k[idx["200"]], k[idx["020"]], k[idx["002"]] = k200, k200 - n7, k200 - n8
+        k[idx["000"]] = rho
+        kt = o.relax_central(k, rho, u, (0, 0, 0), gr)
+        t7 = kt[idx["200"]] - kt[idx["020"]]
+        t8 = kt[idx["200"]] - kt[idx["002"]]
+        t9 = kt[idx["200"]] + kt[idx["020"]] + kt[idx["002"]] - 3 * cs2 * rho
+        # k~ = k + w (k_eq - k)  ->  k_eq = (k~ - (1 - w) k) / w
+        assert (t7 - (1 - wn) * n7) / wn == pytest.approx(q7, rel=1e-9, abs=1e-15)
+        assert (t8 - (1 - wn) * n8) / wn == pytest.approx(q8, rel=1e-9, abs=1e-15)
+        assert (t9 - (1 - wb) * n9) / wb == pytest.approx(q9, rel=1e-9, abs=1e-15)
