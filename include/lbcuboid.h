@@ -191,6 +191,28 @@ lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2
 lb_status lb_collide_vjp(lb_ctx *ctx, long long n, const void *f, const void *F, const void *lam, void *f_bar,
                          void *F_bar, double w_bar[2]);
 
+/* FP64 sums out[0] = sum rho and out[1..3] = sum rho u (rho u = sum f e + F/2)
+ * of n nodes, from pre-collision populations f [27][n] (device memory, natural
+ * layout as returned by lb_get_populations; real_size 4 = float, 8 = double), for
+ * a lattice with aspect ratios r_y, r_z and the uniform body force `force` (NULL =
+ * none).  This entry point has no counterpart in the paper: it is the reduction of
+ * lb_reduce for callers that cannot allocate device memory -- code recorded into
+ * a CUDA graph that may not allocate, hosts whose framework owns all device
+ * memory through its own pool, real-time loops that must never enter the driver
+ * allocator.  It calls no cudaMalloc or cudaFree: its per-block partial sums and
+ * status word live in one fixed array in the library's device globals (about
+ * 131 KB, held by every GPU that loads the library until the process exits), so
+ * n is limited to 134,217,728 nodes (LB_EINVAL beyond).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller; the array keeps the last call's
+ * contents.  Work is issued on `stream` (cudaStream_t, NULL = default stream) and
+ * the call synchronises it.  Returns LB_EUNSTABLE (sums still written) if a node
+ * has a non-finite or non-positive density. */
+lb_status lb_reduce_populations_noalloc(const void *f, int real_size, long long n, double r_y, double r_z,
+                                        const double force[3], double out[4], void *stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *lb_last_error(void);
 

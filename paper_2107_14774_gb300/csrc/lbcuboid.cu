@@ -579,6 +579,8 @@ const char *lb_last_error(void) { return g_last_error.c_str(); }
 
 namespace lbc {
 
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
 __global__ void __launch_bounds__(kReduceThreads)
 k_reduce_final(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
 {
