@@ -138,7 +138,7 @@ def run_ours(args, rank, world):
     kernel_ms = {}
     for var in variants:
         lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var,
-                      corr=w["corr"], stream=stream, device=dev)
+                      corr=w["corr"], stream=stream, device=dev, kernel=args.kernel)
         with torch.cuda.stream(stream):
             lat.init(rho_t, u_t)
             lat.step(args.warmup)
@@ -275,6 +275,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default=",".join(VARIANTS),
                     help="storage forms to time (comma list of f32,f32s,bf16s,f16s,f64)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one"],
+                    help="kernel selection passed to the library (auto = row-staged where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")
     args = ap.parse_args()

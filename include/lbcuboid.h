@@ -96,8 +96,9 @@ typedef struct {
     double lid_u;          /* velocity along x of the wall at j = ny - 1/2 (needs LB_WALL_Y);
                               momentum-augmented bounce-back (Sec. 4, Eq. 69); 0 = at rest */
     void *stream;          /* cudaStream_t to issue all work on; NULL = the legacy default stream */
-    int kernel;            /* 0: automatic (two nodes per thread where the lattice allows it);
-                              1: always one node per thread (for cross-checks) */
+    int kernel;            /* 0: automatic (row-staged kernel or two nodes per thread where the
+                              lattice allows it); 1: one node per thread; 2: two nodes per
+                              thread without staging (cross-checks and measurements) */
 } lb_config;
 
 /* Fill *cfg with defaults: FP32 storage, LOCAL corrections, periodic, no
@@ -145,7 +146,8 @@ lb_status lb_moments(lb_ctx *ctx, void *rho, void *u);
 /* FP64 global sums out[0] = sum rho, out[1..3] = sum rho u (host array), computed
  * with a deterministic two-pass reduction.  Returns LB_EUNSTABLE (with the sums
  * still written) if any node has a non-finite or non-positive density or a
- * non-finite velocity.  Synchronises. */
+ * non-finite velocity, and LB_ETIMEOUT if a bounded wait inside a step kernel ran
+ * out since the context was created (the state is then not valid).  Synchronises. */
 lb_status lb_reduce(lb_ctx *ctx, double out_mass_momentum[4]);
 
 /* Copy the pre-collision populations f_a(x, t) [27][N] (real) out of / into the

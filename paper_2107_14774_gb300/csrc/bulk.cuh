@@ -1,0 +1,245 @@
+// bulk.cuh -- persistent, warp-specialised variant of the fused step: a producer
+// warp streams the 27 source rows of each lattice row into shared memory with
+// bulk asynchronous copies (cp.async.bulk + mbarrier transaction counts), while
+// the consumer warps collide from shared memory and store to global memory.
+//
+// Row-wise staging fits the pull layout exactly: for an x-row (j, k) of the
+// destination, direction a needs the whole source row (j - e_ay, k - e_az) of
+// array a (periodic y/z wrap folded into the row index; across a y or z wall the
+// row (j, k) of array opp(a)), shifted by -e_ax along x with periodic wrap, which
+// is an index shift inside shared memory.  Every global byte is read once, the
+// copies are 16-byte aligned contiguous rows, and no thread holds registers for
+// loads in flight.
+//
+// Every mbarrier wait is bounded: after kSpinLimit polls the thread records an
+// error code in *err and leaves (the producer first waits, again bounded, for
+// the copies it has issued), so a lost arrival can never hang the GPU.
+#pragma once
+
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace lbc {
+
+constexpr int kBulkConsumerWarps = 8;
+constexpr int kBulkThreads = 32 * (kBulkConsumerWarps + 1);
+constexpr unsigned kSpinLimit = 1u << 24;
+
+enum : int { kErrNone = 0, kErrFullWait = 1, kErrEmptyWait = 2 };
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Asynchronous copy of `bytes` (multiple of 16, 16-byte aligned ends) from global
+// memory to shared memory, completing `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory element of the staged rows: 16-bit words for the half formats.
+template <int ST> struct BulkIO;
+template <> struct BulkIO<LB_F32> {
+    using S = float;
+    static __device__ __forceinline__ F2 ld2(const char *row, unsigned xa, unsigned xb, float w, float)
+    {
+        return F2(*reinterpret_cast<const float *>(row + 4u * xa), *reinterpret_cast<const float *>(row + 4u * xb)) -
+               F2(w);
+    }
+    static __device__ __forceinline__ F2 ld2a(const char *row, unsigned x, float w, float)
+    {
+        return F2(*reinterpret_cast<const float2 *>(row + 4u * x)) - F2(w);
+    }
+};
+template <> struct BulkIO<LB_F32_SHIFTED> {
+    using S = float;
+    static __device__ __forceinline__ F2 ld2(const char *row, unsigned xa, unsigned xb, float, float)
+    {
+        return F2(*reinterpret_cast<const float *>(row + 4u * xa), *reinterpret_cast<const float *>(row + 4u * xb));
+    }
+    static __device__ __forceinline__ F2 ld2a(const char *row, unsigned x, float, float)
+    {
+        return F2(*reinterpret_cast<const float2 *>(row + 4u * x));
+    }
+};
+template <> struct BulkIO<LB_F16_SHIFTED> {
+    using S = __half;
+    static __device__ __forceinline__ F2 ld2(const char *row, unsigned xa, unsigned xb, float, float iscale)
+    {
+        const __half a = *reinterpret_cast<const __half *>(row + 2u * xa);
+        const __half b = *reinterpret_cast<const __half *>(row + 2u * xb);
+        return F2(__half2float(a), __half2float(b)) * F2(iscale);
+    }
+    static __device__ __forceinline__ F2 ld2a(const char *row, unsigned x, float, float iscale)
+    {
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(row + 2u * x))) * F2(iscale);
+    }
+};
+template <> struct BulkIO<LB_BF16_SHIFTED> {
+    using S = __nv_bfloat16;
+    static __device__ __forceinline__ F2 ld2(const char *row, unsigned xa, unsigned xb, float, float)
+    {
+        const unsigned a = *reinterpret_cast<const unsigned short *>(row + 2u * xa);
+        const unsigned b = *reinterpret_cast<const unsigned short *>(row + 2u * xb);
+        return F2(__uint_as_float(a << 16), __uint_as_float(b << 16));
+    }
+    static __device__ __forceinline__ F2 ld2a(const char *row, unsigned x, float, float)
+    {
+        const unsigned r = *reinterpret_cast<const unsigned *>(row + 2u * x);
+        return F2(__uint_as_float(r << 16), __uint_as_float(r & 0xffff0000u));
+    }
+};
+
+// Bytes of one staged row slot (rows of up to NXMAX elements) and of one stage.
+template <int ST, int NXMAX>
+struct BulkGeom {
+    static constexpr unsigned elem = sizeof(typename Codec<ST>::S);
+    static constexpr unsigned row = NXMAX * elem;
+    static constexpr unsigned stage = Q * row;
+};
+
+// Shared memory: NS stages of 27 rows, then 2 NS mbarriers (full, empty).
+template <int ST, int CORR, int NXMAX, int NS>
+__global__ void __launch_bounds__(kBulkThreads, 1)
+k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
+            float F2s, const float *__restrict__ ff, int *__restrict__ err)
+{
+    using G = BulkGeom<ST, NXMAX>;
+    using IO = PairIO<ST>;
+    using BI = BulkIO<ST>;
+    extern __shared__ __align__(128) char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NS * G::stage);
+    uint64_t *empty = full + NS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned nx = (unsigned)g.nx;
+    const long long nrows = (long long)g.ny * g.nz;
+    const unsigned rowbytes = nx * G::elem;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kBulkConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kBulkConsumerWarps) {
+        // ---------------- producer ----------------
+        if (lane != 0) return;
+        long long n = 0;
+        for (long long r = blockIdx.x; r < nrows; r += gridDim.x, ++n) {
+            const int s = (int)(n % NS);
+            if (n >= NS && !mbar_wait_bounded(&empty[s], (unsigned)(((n / NS) - 1) & 1))) {
+                atomicExch(err, kErrEmptyWait);
+                break;
+            }
+            const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+            int ys[3], zs[3];
+            bool yo[3], zo[3];
+            axis_sources(j, g.ny, g.wall[1], ys, yo);
+            axis_sources(k, g.nz, g.wall[2], zs, zo);
+            mbar_arrive_expect_tx(&full[s], Q * rowbytes);
+            char *stage = smem + s * G::stage;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const int cy = ey(a) + 1, cz = ez(a) + 1;
+                const typename Codec<ST>::S *src;
+                if (yo[cy] | zo[cz])   // half-way bounce-back: row (j, k) of the opposite direction
+                    src = ptr.src[opp(a)] + ((long long)k * g.ny + j) * nx;
+                else
+                    src = ptr.src[a] + ((long long)zs[cz] * g.ny + ys[cy]) * nx;
+                bulk_g2s(stage + a * G::row, src, rowbytes, &full[s]);
+            }
+        }
+        // before leaving, let the copies issued for the last stages land (bounded)
+        const long long issued = n;
+        for (long long m = (issued > NS ? issued - NS : 0); m < issued; ++m)
+            if (!mbar_wait_bounded(&full[m % NS], (unsigned)((m / NS) & 1))) break;
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const unsigned tid = threadIdx.x;   // 0 .. 32 * kBulkConsumerWarps - 1
+    long long n = 0;
+    for (long long r = blockIdx.x; r < nrows; r += gridDim.x, ++n) {
+        const int s = (int)(n % NS);
+        if (!mbar_wait_bounded(&full[s], (unsigned)((n / NS) & 1))) {
+            atomicExch(err, kErrFullWait);
+            return;
+        }
+        const char *stage = smem + s * G::stage;
+        const unsigned rowoff = (unsigned)r * nx;
+        for (unsigned i0 = 2 * tid; i0 < nx; i0 += 2 * 32 * kBulkConsumerWarps) {
+            const unsigned xm = (i0 == 0) ? nx - 1u : i0 - 1u;       // source of ex = +1 for node i0
+            const unsigned xp = (i0 + 2 == nx) ? 0u : i0 + 2u;       // source of ex = -1 for node i0+1
+            F2 h[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const char *row = stage + a * G::row;
+                if (ex(a) == 0)
+                    h[a] = BI::ld2a(row, i0, D.w[a], D.iscale[a]);
+                else if (ex(a) == 1)
+                    h[a] = BI::ld2(row, xm, i0, D.w[a], D.iscale[a]);
+                else
+                    h[a] = BI::ld2(row, i0 + 1, xp, D.w[a], D.iscale[a]);
+            }
+            const unsigned self = rowoff + i0;
+            F2 Fx(F0), Fy(F1), Fz(F2s);
+            if (ff) {
+                const unsigned N = (unsigned)g.N;
+                Fx += F2(__ldg(reinterpret_cast<const float2 *>(ff + self)));
+                Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
+                Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
+            }
+            collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy,
+                               Fz);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+}  // namespace lbc

@@ -175,87 +175,97 @@ struct PostState {
 // O(u^2) corrections and the density, well inside the FP32 error budget).
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_(float a, float b) { return a * __frcp_rn(b); }
+__device__ __forceinline__ F2 div_(F2 a, F2 b) { return F2(div_(a.v.x, b.v.x), div_(a.v.y, b.v.y)); }
 
-// Relaxation of one node (App. D) from its raw moments.  F: body force at the
-// node; gr: density gradient (used by LB_CORR_FULL only).
-template <class T, int CORR>
-__device__ __forceinline__ PostState<T> relax_node(const RawMoments<T> &m, const Phys<T> &P, T Fx, T Fy, T Fz,
-                                                   T grx, T gry, T grz)
+// Relaxation of one node (App. D) from its raw moments (V = float/double for one
+// node, F2 for two nodes in packed lanes).  F: body force at the node; gr:
+// density gradient (used by LB_CORR_FULL only).
+template <class V, int CORR>
+__device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const Phys<typename Scalar<V>::type> &P,
+                                                   V Fx, V Fy, V Fz, V grx, V gry, V grz)
 {
-    const T cs2 = P.cs2;
-    const T dr = m.dr;
-    const T rho = T(1) + dr;
-    const T irho = div_(T(1), rho);
+    using T = typename Scalar<V>::type;
+    const V cs2 = V(P.cs2);
+    const V half = V(T(0.5));
+    const V dr = m.dr;
+    const V rho = V(T(1)) + dr;
+    const V irho = div_(V(T(1)), rho);
     // rho u = sum f e + F/2 (Eq. 12)
-    const T ux = (m.jx + T(0.5) * Fx) * irho;
-    const T uy = (m.jy + T(0.5) * Fy) * irho;
-    const T uz = (m.jz + T(0.5) * Fz) * irho;
+    const V ux = fma_(half, Fx, m.jx) * irho;
+    const V uy = fma_(half, Fy, m.jy) * irho;
+    const V uz = fma_(half, Fz, m.jz) * irho;
 
     // second-order central moments (App. C), diagonal ones as deviations from cs2 rho:
     // k_200 - cs2 rho = sum h ex^2 - cs2 (rho - 1) - rho ux^2 + ux Fx, etc.
-    const T n200 = m.pxx - cs2 * dr - rho * ux * ux + ux * Fx;
-    const T n020 = m.pyy - cs2 * dr - rho * uy * uy + uy * Fy;
-    const T n002 = m.pzz - cs2 * dr - rho * uz * uz + uz * Fz;
-    const T k110 = m.pxy - rho * ux * uy + T(0.5) * (ux * Fy + uy * Fx);
-    const T k101 = m.pxz - rho * ux * uz + T(0.5) * (ux * Fz + uz * Fx);
-    const T k011 = m.pyz - rho * uy * uz + T(0.5) * (uy * Fz + uz * Fy);
+    const V rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
+    const V n200 = fma_(ux, Fx - rux, m.pxx - cs2 * dr);
+    const V n020 = fma_(uy, Fy - ruy, m.pyy - cs2 * dr);
+    const V n002 = fma_(uz, Fz - ruz, m.pzz - cs2 * dr);
+    const V k110 = m.pxy - rux * uy + half * (ux * Fy + uy * Fx);
+    const V k101 = m.pxz - rux * uz + half * (ux * Fz + uz * Fx);
+    const V k011 = m.pyz - ruy * uz + half * (uy * Fz + uz * Fy);
 
     // B: combined diagonal moments (App. D); N2s = k_2s - 3 cs2 rho
-    const T N2s = n200 + n020 + n002;
-    const T k2d1 = n200 - n020;
-    const T k2d2 = n200 - n002;
+    const V N2s = n200 + n020 + n002;
+    const V k2d1 = n200 - n020;
+    const V k2d2 = n200 - n002;
 
     // corrected equilibria of the combined moments (App. D, Eq. 63), as deviations
-    T E2s = T(0), E2d1 = T(0), E2d2 = T(0);
+    V E2s = V(T(0)), E2d1 = V(T(0)), E2d2 = V(T(0));
     if (CORR != LB_CORR_NONE) {
-        const T al = (CORR == LB_CORR_LOWMACH) ? T(0) : T(1);
-        const T ux2 = al * ux * ux, uy2 = al * uy * uy, uz2 = al * uz * uz;
+        const V al = V((CORR == LB_CORR_LOWMACH) ? T(0) : T(1));
+        const V ux2 = al * ux * ux, uy2 = al * uy * uy, uz2 = al * uz * uz;
+        const V an0 = V(P.an[0]), an1 = V(P.an[1]), an2 = V(P.an[2]);
         // density-gradient terms (FULL only): A, B, C and e-terms
-        T ebr = T(0), esr1 = T(0), esr2 = T(0);
+        V ebr = V(T(0)), esr1 = V(T(0)), esr2 = V(T(0));
         if (CORR == LB_CORR_FULL) {
-            const T A = T(0.5) * P.an[0] * ux, B = T(0.5) * P.an[1] * uy, C = T(0.5) * P.an[2] * uz;
+            const V A = half * an0 * ux, B = half * an1 * uy, C = half * an2 * uz;
             esr1 = -A * grx + B * gry;
             esr2 = -A * grx + C * grz;
             ebr = -A * grx - B * gry - C * grz;
         }
-        const T Rb = N2s + ebr, Rs1 = k2d1 + esr1, Rs2 = k2d2 + esr2;
-        const T hx = T(0.5) * P.an[0] + T(1.5) * ux2;
-        const T hy = T(0.5) * P.an[1] + T(1.5) * uy2;
-        const T hz = T(0.5) * P.an[2] + T(1.5) * uz2;
-        const T Csx = (hx - P.two_cs2_wn) * rho;
-        const T Cbx = (hx - P.two_cs2_wb) * rho;
-        const T Csy = (P.two_cs2_wn - hy) * rho;
-        const T Cby = (hy - P.two_cs2_wb) * rho;
-        const T Csz = (P.two_cs2_wn - hz) * rho;
-        const T Cbz = (hz - P.two_cs2_wb) * rho;
+        const V Rb = N2s + ebr, Rs1 = k2d1 + esr1, Rs2 = k2d2 + esr2;
+        const V onep5 = V(T(1.5));
+        const V hx = fma_(onep5, ux2, half * an0);
+        const V hy = fma_(onep5, uy2, half * an1);
+        const V hz = fma_(onep5, uz2, half * an2);
+        const V c2n = V(P.two_cs2_wn), c2b = V(P.two_cs2_wb);
+        const V Csx = (hx - c2n) * rho;
+        const V Cbx = (hx - c2b) * rho;
+        const V Csy = (c2n - hy) * rho;
+        const V Cby = (hy - c2b) * rho;
+        const V Csz = (c2n - hz) * rho;
+        const V Cbz = (hz - c2b) * rho;
         // Eq. 49 / App. D: Cramer's rule on the 3x3 system
-        const T num = -Csz * Cby * Rs1 - Csy * (Cbz * Rs2 - Csz * Rb);
-        const T den = -Csx * Csz * Cby - Csy * (Csx * Cbz - Csz * Cbx);
-        const T dxux = div_(num, den);
-        const T dyuy = div_(Rs1 - Csx * dxux, Csy);
-        const T dzuz = div_(Rs2 - Csx * dxux, Csz);
+        const V num = -Csz * Cby * Rs1 - Csy * (Cbz * Rs2 - Csz * Rb);
+        const V den = -Csx * Csz * Cby - Csy * (Csx * Cbz - Csz * Cbx);
+        const V dxux = div_(num, den);
+        const V dyuy = div_(Rs1 - Csx * dxux, Csy);
+        const V dzuz = div_(Rs2 - Csx * dxux, Csz);
         // theta coefficients (Eq. 38-40 in the shear/bulk notation of App. D)
-        const T qx = -rho * (T(3) * ux2 + P.an[0]);
-        const T qy = -rho * (T(3) * uy2 + P.an[1]);
-        const T qz = -rho * (T(3) * uz2 + P.an[2]);
-        E2s = P.tb * (qx * dxux + qy * dyuy + qz * dzuz);
-        E2d1 = P.tn * (qx * dxux - qy * dyuy);
-        E2d2 = P.tn * (qx * dxux - qz * dzuz);
+        const V three = V(T(3));
+        const V qx = -rho * fma_(three, ux2, an0);
+        const V qy = -rho * fma_(three, uy2, an1);
+        const V qz = -rho * fma_(three, uz2, an2);
+        const V tb = V(P.tb), tn = V(P.tn);
+        E2s = tb * (qx * dxux + qy * dyuy + qz * dzuz);
+        E2d1 = tn * (qx * dxux - qy * dyuy);
+        E2d2 = tn * (qx * dxux - qz * dzuz);
         if (CORR == LB_CORR_FULL) {
             // lambda coefficients: s-terms -, +, + ; b-terms -, -, -
-            const T lx = P.an[0] * ux, ly = P.an[1] * uy, lz = P.an[2] * uz;
-            E2s -= P.tb * (lx * grx + ly * gry + lz * grz);
-            E2d1 += P.tn * (-lx * grx + ly * gry);
-            E2d2 += P.tn * (-lx * grx + lz * grz);
+            const V lx = an0 * ux, ly = an1 * uy, lz = an2 * uz;
+            E2s -= tb * (lx * grx + ly * gry + lz * grz);
+            E2d1 += tn * (-lx * grx + ly * gry);
+            E2d2 += tn * (-lx * grx + lz * grz);
         }
     }
     // relaxation (App. D)
-    const T wn = P.wn, wb = P.wb;
-    const T t2s = N2s + wb * (E2s - N2s);
-    const T t2d1 = k2d1 + wn * (E2d1 - k2d1);
-    const T t2d2 = k2d2 + wn * (E2d2 - k2d2);
-    const T onemw = T(1) - wn;
-    PostState<T> o;
+    const V wn = V(P.wn), wb = V(P.wb);
+    const V t2s = fma_(wb, E2s - N2s, N2s);
+    const V t2d1 = fma_(wn, E2d1 - k2d1, k2d1);
+    const V t2d2 = fma_(wn, E2d2 - k2d2, k2d2);
+    const V onemw = V(T(1) - P.wn);
+    PostState<V> o;
     o.dr = dr;
     o.ux = ux;
     o.uy = uy;
@@ -264,19 +274,22 @@ __device__ __forceinline__ PostState<T> relax_node(const RawMoments<T> &m, const
     o.t101 = onemw * k101;
     o.t011 = onemw * k011;
     // B^-1 (end of App. D), deviations of k~_200, k~_020, k~_002 from cs2 rho
-    const T third = T(1) / T(3);
+    const V third = V(T(1) / T(3));
+    const V two = V(T(2));
     o.d200 = (t2s + t2d1 + t2d2) * third;
-    o.d020 = (t2s - T(2) * t2d1 + t2d2) * third;
-    o.d002 = (t2s + t2d1 - T(2) * t2d2) * third;
-    o.hFx = T(0.5) * Fx;
-    o.hFy = T(0.5) * Fy;
-    o.hFz = T(0.5) * Fz;
+    o.d020 = (t2s - two * t2d1 + t2d2) * third;
+    o.d002 = (t2s + t2d1 - two * t2d2) * third;
+    o.hFx = half * Fx;
+    o.hFy = half * Fy;
+    o.hFz = half * Fz;
     return o;
 }
 
 // Back to populations: h~ = f^eq(rho, u) - w + M(u)^-1 (k~ - k^eq) (Apps. E-G).
-template <class V, class T>
-__device__ __forceinline__ void back_transform(V (&h)[Q], const PostState<V> &o, const Phys<T> &P)
+// Each post-collision deviation is handed to out(a, value) as soon as it is
+// formed (a store, or a write into a register array).
+template <class V, class T, class Out>
+__device__ __forceinline__ void back_transform_to(Out &&out, const PostState<V> &o, const Phys<T> &P)
 {
     const AxisCols<V> X = axis_cols(o.ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0]);
     const AxisCols<V> Y = axis_cols(o.uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]);
@@ -310,9 +323,15 @@ __device__ __forceinline__ void back_transform(V (&h)[Q], const PostState<V> &o,
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
                 const V heq = fma_(ax[x], Pyz, X.w[x] * Dyz);
-                h[dir_of(x - 1, y - 1, z - 1)] = fma_(B0, X.g0[x], fma_(B1, X.g1[x], fma_(B2, X.g2[x], heq)));
+                out(dir_of(x - 1, y - 1, z - 1), fma_(B0, X.g0[x], fma_(B1, X.g1[x], fma_(B2, X.g2[x], heq))));
             }
         }
+}
+
+template <class V, class T>
+__device__ __forceinline__ void back_transform(V (&h)[Q], const PostState<V> &o, const Phys<T> &P)
+{
+    back_transform_to([&](int a, V v) { h[a] = v; }, o, P);
 }
 
 // One collision, in place on the deviations h of one node (Sec. 3.2 steps, App. D).
@@ -333,23 +352,13 @@ __device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T F
 
 // Two collisions (two nodes in the lanes of F2), in place.  The linear transforms
 // run in packed FP32x2 instructions; the per-node relaxation runs per lane.
-template <int CORR>
-__device__ __forceinline__ void collide_pair(F2 (&h)[Q], const Phys<float> &P, F2 F0, F2 F1, F2 F2_)
+template <int CORR, class Out>
+__device__ __forceinline__ void collide_pair(const F2 (&h)[Q], Out &&out, const Phys<float> &P, F2 F0, F2 F1, F2 F2_)
 {
     const RawMoments<F2> m = raw_moments(h, P);
-    RawMoments<float> a, b;
-#define LBC_SPLIT(f) a.f = m.f.v.x; b.f = m.f.v.y;
-    LBC_SPLIT(dr) LBC_SPLIT(jx) LBC_SPLIT(jy) LBC_SPLIT(jz) LBC_SPLIT(pxx) LBC_SPLIT(pyy) LBC_SPLIT(pzz)
-    LBC_SPLIT(pxy) LBC_SPLIT(pxz) LBC_SPLIT(pyz)
-#undef LBC_SPLIT
-    const PostState<float> oa = relax_node<float, CORR>(a, P, F0.v.x, F1.v.x, F2_.v.x, 0.f, 0.f, 0.f);
-    const PostState<float> ob = relax_node<float, CORR>(b, P, F0.v.y, F1.v.y, F2_.v.y, 0.f, 0.f, 0.f);
-    PostState<F2> o;
-#define LBC_JOIN(f) o.f = F2(oa.f, ob.f);
-    LBC_JOIN(dr) LBC_JOIN(ux) LBC_JOIN(uy) LBC_JOIN(uz) LBC_JOIN(hFx) LBC_JOIN(hFy) LBC_JOIN(hFz)
-    LBC_JOIN(t110) LBC_JOIN(t101) LBC_JOIN(t011) LBC_JOIN(d200) LBC_JOIN(d020) LBC_JOIN(d002)
-#undef LBC_JOIN
-    back_transform(h, o, P);
+    const F2 z(0.f);
+    const PostState<F2> o = relax_node<F2, CORR>(m, P, F0, F1, F2_, z, z, z);
+    back_transform_to(out, o, P);
 }
 
 // Equilibrium deviations h^eq_a = f^eq_a(rho, u) - w_a (init and moving walls).

@@ -210,44 +210,64 @@ k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__r
 // Requirements (checked on the host): nx even, no walls normal to x, no moving
 // lid, corrections other than FULL.
 
+// Raw stored pair of two x-adjacent values (what the loads return) and its
+// decoding into deviations h, per storage type.  Keeping the raw words lets a
+// thread hold the next plane's loads in flight while it computes the current one.
 template <int ST> struct PairIO;
 template <> struct PairIO<LB_F32> {
     using S = float;
-    static __device__ __forceinline__ F2 load2(const S *p, float w, float)
-    {
-        return F2(__ldg(reinterpret_cast<const float2 *>(p))) - F2(w);
-    }
-    static __device__ __forceinline__ void store2(S *p, F2 h, float w, float)
+    using Raw = float2;
+    static __device__ __forceinline__ Raw ld2(const S *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ Raw ld11(const S *p0, const S *p1) { return make_float2(__ldg(p0), __ldg(p1)); }
+    static __device__ __forceinline__ F2 dec(Raw r, float w, float) { return F2(r) - F2(w); }
+    static __device__ __forceinline__ void st2(S *p, F2 h, float w, float)
     {
         *reinterpret_cast<float2 *>(p) = (h + F2(w)).v;
     }
 };
 template <> struct PairIO<LB_F32_SHIFTED> {
     using S = float;
-    static __device__ __forceinline__ F2 load2(const S *p, float, float)
-    {
-        return F2(__ldg(reinterpret_cast<const float2 *>(p)));
-    }
-    static __device__ __forceinline__ void store2(S *p, F2 h, float, float) { *reinterpret_cast<float2 *>(p) = h.v; }
+    using Raw = float2;
+    static __device__ __forceinline__ Raw ld2(const S *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ Raw ld11(const S *p0, const S *p1) { return make_float2(__ldg(p0), __ldg(p1)); }
+    static __device__ __forceinline__ F2 dec(Raw r, float, float) { return F2(r); }
+    static __device__ __forceinline__ void st2(S *p, F2 h, float, float) { *reinterpret_cast<float2 *>(p) = h.v; }
 };
+// 16-bit forms: the raw word holds the element at the lower address in its low half.
+__device__ __forceinline__ unsigned ld16x2(const void *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
+__device__ __forceinline__ unsigned ld16_16(const void *p0, const void *p1)
+{
+    const unsigned lo = __ldg(reinterpret_cast<const unsigned short *>(p0));
+    const unsigned hi = __ldg(reinterpret_cast<const unsigned short *>(p1));
+    return __byte_perm(lo, hi, 0x5410);
+}
 template <> struct PairIO<LB_F16_SHIFTED> {
     using S = __half;
-    static __device__ __forceinline__ F2 load2(const S *p, float, float iscale)
+    using Raw = unsigned;
+    static __device__ __forceinline__ Raw ld2(const S *p) { return ld16x2(p); }
+    static __device__ __forceinline__ Raw ld11(const S *p0, const S *p1) { return ld16_16(p0, p1); }
+    static __device__ __forceinline__ F2 dec(Raw r, float, float iscale)
     {
-        return F2(__half22float2(__ldg(reinterpret_cast<const __half2 *>(p)))) * F2(iscale);
+        __half2 v;
+        memcpy(&v, &r, sizeof(v));
+        return F2(__half22float2(v)) * F2(iscale);
     }
-    static __device__ __forceinline__ void store2(S *p, F2 h, float, float scale)
+    static __device__ __forceinline__ void st2(S *p, F2 h, float, float scale)
     {
         *reinterpret_cast<__half2 *>(p) = __float22half2_rn((h * F2(scale)).v);
     }
 };
 template <> struct PairIO<LB_BF16_SHIFTED> {
     using S = __nv_bfloat16;
-    static __device__ __forceinline__ F2 load2(const S *p, float, float)
+    using Raw = unsigned;
+    static __device__ __forceinline__ Raw ld2(const S *p) { return ld16x2(p); }
+    static __device__ __forceinline__ Raw ld11(const S *p0, const S *p1) { return ld16_16(p0, p1); }
+    static __device__ __forceinline__ F2 dec(Raw r, float, float)
     {
-        return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p))));
+        // a bfloat16 is the upper half of the float with the same bits
+        return F2(__uint_as_float(r << 16), __uint_as_float(r & 0xffff0000u));
     }
-    static __device__ __forceinline__ void store2(S *p, F2 h, float, float)
+    static __device__ __forceinline__ void st2(S *p, F2 h, float, float)
     {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(h.v);
     }
@@ -262,61 +282,82 @@ struct DirPtrs {
     S *dst[Q];
 };
 
-template <int ST, int CORR>
-__global__ void __launch_bounds__(kBlockThreads)
-k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
-            float F2s, const float *__restrict__ ff)
+// Issue the loads of the two nodes (i0, i0+1) of row j, plane k.
+template <int ST>
+__device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], const DirPtrs<typename Codec<ST>::S> &ptr,
+                                           const Geom &g, int i0, unsigned xm, unsigned xp, const int (&ys)[3],
+                                           const bool (&yo)[3], int k)
 {
-    using C = Codec<ST>;
     using IO = PairIO<ST>;
-    const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i0 >= g.nx || j >= g.ny) return;
-    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
-    int ys[3], zs[3];
-    bool yo[3], zo[3];
-    axis_sources(j, g.ny, g.wall[1], ys, yo);
+    int zs[3];
+    bool zo[3];
     axis_sources(k, g.nz, g.wall[2], zs, zo);
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
     unsigned rowbase[3][3];
 #pragma unroll
     for (int cy = 0; cy < 3; ++cy)
 #pragma unroll
         for (int cz = 0; cz < 3; ++cz) rowbase[cy][cz] = (unsigned)zs[cz] * nxy + (unsigned)ys[cy] * nx;
     const unsigned self = rowbase[1][1] + (unsigned)i0;
-    const unsigned xm = (i0 == 0) ? nx - 1u : (unsigned)i0 - 1u;       // source of ex = +1 for node i0
-    const unsigned xp = (i0 + 2 == g.nx) ? 0u : (unsigned)i0 + 2u;     // source of ex = -1 for node i0+1
-    F2 h[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
         if (yo[cy] | zo[cz]) {
             // half-way bounce-back across a y or z wall: f_a(x) = S_opp(a)(x) for both nodes
-            h[a] = IO::load2(ptr.src[opp(a)] + self, D.w[a], D.iscale[a]);
+            raw[a] = IO::ld2(ptr.src[opp(a)] + self);
         } else {
             const unsigned rb = rowbase[cy][cz];
-            const typename C::S *p = ptr.src[a];
-            if (cx == 1) {
-                h[a] = IO::load2(p + (rb + (unsigned)i0), D.w[a], D.iscale[a]);
-            } else if (cx == 2) {  // ex = +1: sources i0 - 1, i0
-                h[a] = F2(C::load(__ldg(p + (rb + xm)), D.w[a], D.iscale[a]),
-                          C::load(__ldg(p + (rb + (unsigned)i0)), D.w[a], D.iscale[a]));
-            } else {               // ex = -1: sources i0 + 1, i0 + 2
-                h[a] = F2(C::load(__ldg(p + (rb + (unsigned)i0 + 1u)), D.w[a], D.iscale[a]),
-                          C::load(__ldg(p + (rb + xp)), D.w[a], D.iscale[a]));
-            }
+            const typename Codec<ST>::S *p = ptr.src[a];
+            if (cx == 1)
+                raw[a] = IO::ld2(p + (rb + (unsigned)i0));
+            else if (cx == 2)   // ex = +1: sources i0 - 1, i0
+                raw[a] = IO::ld11(p + (rb + xm), p + (rb + (unsigned)i0));
+            else                // ex = -1: sources i0 + 1, i0 + 2
+                raw[a] = IO::ld11(p + (rb + (unsigned)i0 + 1u), p + (rb + xp));
         }
     }
-    F2 Fx(F0), Fy(F1), Fz(F2s);
-    if (ff) {
-        const unsigned N = (unsigned)g.N;
-        Fx += F2(__ldg(reinterpret_cast<const float2 *>(ff + self)));
-        Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
-        Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
-    }
-    collide_pair<CORR>(h, P, Fx, Fy, Fz);
+}
+
+// ZC consecutive planes per thread: the loads of plane k+1 are issued before the
+// collision of plane k, so that every warp keeps memory requests in flight while
+// it computes (software pipelining across z).
+#ifndef LBC_PAIR_MINBLOCKS
+#define LBC_PAIR_MINBLOCKS 1
+#endif
+template <int ST, int CORR, int ZC>
+__global__ void __launch_bounds__(kBlockThreads, LBC_PAIR_MINBLOCKS)
+k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
+            float F2s, const float *__restrict__ ff)
+{
+    using IO = PairIO<ST>;
+    const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z * ZC;
+    if (i0 >= g.nx || j >= g.ny) return;
+    const int kend = min(k0 + ZC, g.nz);
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    int ys[3];
+    bool yo[3];
+    axis_sources(j, g.ny, g.wall[1], ys, yo);
+    const unsigned xm = (i0 == 0) ? nx - 1u : (unsigned)i0 - 1u;       // source of ex = +1 for node i0
+    const unsigned xp = (i0 + 2 == g.nx) ? 0u : (unsigned)i0 + 2u;     // source of ex = -1 for node i0+1
+    typename IO::Raw raw[Q];
+    pair_fetch<ST>(raw, ptr, g, i0, xm, xp, ys, yo, k0);
+    for (int k = k0; k < kend; ++k) {
+        F2 h[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) IO::store2(ptr.dst[a] + self, h[a], D.w[a], D.scale[a]);
+        for (int a = 0; a < Q; ++a) h[a] = IO::dec(raw[a], D.w[a], D.iscale[a]);
+        if (k + 1 < kend) pair_fetch<ST>(raw, ptr, g, i0, xm, xp, ys, yo, k + 1);
+        const unsigned self = (unsigned)k * nxy + (unsigned)j * nx + (unsigned)i0;
+        F2 Fx(F0), Fy(F1), Fz(F2s);
+        if (ff) {
+            const unsigned N = (unsigned)g.N;
+            Fx += F2(__ldg(reinterpret_cast<const float2 *>(ff + self)));
+            Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
+            Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
+        }
+        collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy, Fz);
+    }
 }
 
 // Density of every node (pre-pass of LB_CORR_FULL).

@@ -73,6 +73,8 @@ struct lb_ctx {
     // lb_init / lb_set_populations (the moving-lid term belongs to streaming after
     // a collision, so it is not applied when those populations are read).
     bool fresh;
+    int *err;               // error word of the bounded waits of the staged kernel
+    int sm_count;
 };
 
 namespace {
@@ -96,7 +98,9 @@ LaunchArgs launch_args(const lb_ctx *c)
     a.stream = c->stream;
     a.force_field = c->force_field;
     a.rho_field = c->rho_field;
-    a.pair_disabled = c->cfg.kernel == 1;
+    a.kernel = c->cfg.kernel;
+    a.err = c->err;
+    a.sm_count = c->sm_count;
     return a;
 }
 
@@ -188,7 +192,7 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (cfg->storage < LB_F64 || cfg->storage > LB_BF16_SHIFTED) return fail(LB_EINVAL, "lb_create_ex: bad storage");
     if (cfg->corr < LB_CORR_NONE || cfg->corr > LB_CORR_FULL) return fail(LB_EINVAL, "lb_create_ex: bad corr");
     if (cfg->wall_mask & ~7u) return fail(LB_EINVAL, "lb_create_ex: bad wall_mask");
-    if (cfg->kernel < 0 || cfg->kernel > 1) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
+    if (cfg->kernel < 0 || cfg->kernel > 2) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
     if (cfg->lid_u != 0.0 && !(cfg->wall_mask & LB_WALL_Y))
         return fail(LB_EINVAL, "lb_create_ex: a moving lid needs walls normal to y");
     const double r = cfg->r_y, s = cfg->r_z;
@@ -233,6 +237,13 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (e == cudaSuccess) e = cudaMalloc(&c->partial, sizeof(double) * 4 * c->nred);
     if (e == cudaSuccess) e = cudaMalloc(&c->out4, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e == cudaSuccess && cfg->corr == LB_CORR_FULL) e = cudaMalloc(&c->rho_field, N * c->rbytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, bytes, c->stream);
@@ -256,6 +267,7 @@ void lb_destroy(lb_ctx *c)
     cudaFree(c->partial);
     cudaFree(c->out4);
     cudaFree(c->status);
+    cudaFree(c->err);
     delete c;
 }
 
@@ -358,7 +370,11 @@ lb_status lb_reduce(lb_ctx *c, double out[4])
     unsigned status = 0;
     LB_CUDA(cudaMemcpyAsync(out, c->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    int err = 0;
+    LB_CUDA(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
+    if (err) return fail(LB_ETIMEOUT, "lb_reduce: a bounded wait of the staged step kernel ran out (code " +
+                                          std::to_string(err) + "); the state is not valid");
     if (status) return fail(LB_EUNSTABLE, "lb_reduce: non-finite or non-positive density/velocity found");
     return LB_OK;
 }

@@ -5,8 +5,11 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "adjoint.cuh"
+#include "bulk.cuh"
 
 namespace lbc {
 
@@ -22,8 +25,16 @@ struct LaunchArgs {
     cudaStream_t stream;
     const void *force_field;  // device, compute type, [3][N] or null
     void *rho_field;          // device, compute type, [N] (FULL) or null
-    bool pair_disabled;       // force the one-node kernel (tests compare both)
+    int kernel;               // 0 automatic, 1 one node per thread, 2 two nodes per thread
+    int *err;                 // device error word of the bounded waits (bulk kernel)
+    int sm_count;             // multiprocessors of the device
 };
+
+#ifndef LBC_PAIR_PLANES
+#define LBC_PAIR_PLANES 8
+#endif
+// z-planes per thread of the two-node kernel (software pipelining depth).
+constexpr int kPairPlanes = LBC_PAIR_PLANES;
 
 inline void launch_shape(const Geom &g, dim3 &grid, dim3 &block)
 {
@@ -55,6 +66,8 @@ struct Ops {
     static cudaError_t step(const LaunchArgs &a, const void *src, void *dst);
     static bool use_pair(const LaunchArgs &a);
     static cudaError_t step_pair(const LaunchArgs &a, const void *src, void *dst);
+    static bool use_bulk(const LaunchArgs &a);
+    static cudaError_t step_bulk(const LaunchArgs &a, const void *src, void *dst);
     static cudaError_t gather(const LaunchArgs &a, const void *src, void *rho, void *u, void *f);
     static cudaError_t scatter(const LaunchArgs &a, void *dst, const void *rho, const void *u, const void *f);
     static cudaError_t reduce_partial(const LaunchArgs &a, const void *src, double *partial, int nblocks,
@@ -89,6 +102,7 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
     if (a.corr == LB_CORR_FULL) {
         k_density<ST><<<grid, block, 0, a.stream>>>(s, a.g, P, D, (T)a.lid_u, rf);
     }
+    if (use_bulk(a)) return step_bulk(a, src, dst);
     if (use_pair(a)) return step_pair(a, src, dst);
     switch (a.corr) {
     case LB_CORR_NONE:
@@ -117,7 +131,7 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
 template <int ST>
 bool Ops<ST>::use_pair(const LaunchArgs &a)
 {
-    if (ST == LB_F64 || a.pair_disabled) return false;
+    if (ST == LB_F64 || a.kernel == 1) return false;
     return (a.g.nx % 2 == 0) && !a.g.wall[0] && a.lid_u == 0.0 && a.corr != LB_CORR_FULL &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
@@ -128,11 +142,12 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
     if constexpr (ST == LB_F64) {
         return cudaErrorInvalidValue;
     } else {
+        constexpr int ZC = kPairPlanes;
         const int np = a.g.nx / 2;
         int bx = kBlockX;
         while (bx > 1 && bx / 2 >= np) bx /= 2;
         const int by = kBlockThreads / bx;
-        const dim3 block(bx, by, 1), grid((np + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
+        const dim3 block(bx, by, 1), grid((np + bx - 1) / bx, (a.g.ny + by - 1) / by, (a.g.nz + ZC - 1) / ZC);
         const Phys<float> P = phys(a);
         const DirConst<float> D = dirs(a);
         DirPtrs<S> ptr;
@@ -144,16 +159,71 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
         const float F0 = (float)a.F[0], F1 = (float)a.F[1], F2 = (float)a.F[2];
         switch (a.corr) {
         case LB_CORR_NONE:
-            k_step_pair<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            k_step_pair<ST, LB_CORR_NONE, ZC><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
             break;
         case LB_CORR_LOWMACH:
-            k_step_pair<ST, LB_CORR_LOWMACH><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            k_step_pair<ST, LB_CORR_LOWMACH, ZC><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
             break;
         default:
-            k_step_pair<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            k_step_pair<ST, LB_CORR_LOCAL, ZC><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
             break;
         }
         return cudaGetLastError();
+    }
+}
+
+// The staged (bulk-copy) kernel: FP32-arithmetic storage, LOCAL corrections,
+// rows of at most 1024 elements whose byte length is a multiple of 16, no walls
+// normal to x, no moving lid.
+template <int ST>
+bool Ops<ST>::use_bulk(const LaunchArgs &a)
+{
+    if (ST == LB_F64 || a.kernel != 0 || a.corr != LB_CORR_LOCAL || !a.err) return false;
+    const unsigned elem = (unsigned)sizeof(S);
+    return a.g.nx >= 2 && a.g.nx <= 1024 && (a.g.nx * elem) % 16 == 0 && !a.g.wall[0] && a.lid_u == 0.0 &&
+           (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
+}
+
+template <int ST, int NXMAX, int NS>
+cudaError_t launch_bulk(const LaunchArgs &a, const void *src, void *dst)
+{
+    using S = typename Codec<ST>::S;
+    constexpr size_t smem = (size_t)NS * BulkGeom<ST, NXMAX>::stage + 2 * NS * sizeof(uint64_t);
+    auto kern = k_step_bulk<ST, LB_CORR_LOCAL, NXMAX, NS>;
+    static bool configured = false;   // per instantiation; the attribute is per device function
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    DirPtrs<S> ptr;
+    for (int q = 0; q < Q; ++q) {
+        ptr.src[q] = static_cast<const S *>(src) + (size_t)q * (size_t)a.g.N;
+        ptr.dst[q] = static_cast<S *>(dst) + (size_t)q * (size_t)a.g.N;
+    }
+    const Phys<float> P = make_phys<float>(a.r, a.s, a.cs2, a.wn, a.wb);
+    DirConst<float> D;
+    for (int q = 0; q < Q; ++q) {
+        D.w[q] = (float)a.w[q];
+        D.scale[q] = a.scale[q];
+        D.iscale[q] = 1.0f / a.scale[q];
+    }
+    const long long rows = (long long)a.g.ny * a.g.nz;
+    const int grid = (int)std::min<long long>(rows, (long long)a.sm_count);
+    kern<<<grid, kBulkThreads, smem, a.stream>>>(ptr, a.g, P, D, (float)a.F[0], (float)a.F[1], (float)a.F[2],
+                                                 static_cast<const float *>(a.force_field), a.err);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Ops<ST>::step_bulk(const LaunchArgs &a, const void *src, void *dst)
+{
+    if constexpr (ST == LB_F64) {
+        return cudaErrorInvalidValue;
+    } else {
+        constexpr bool wide = sizeof(S) == 4;
+        if (a.g.nx <= 512) return launch_bulk<ST, 512, wide ? 3 : 4>(a, src, dst);
+        return launch_bulk<ST, 1024, wide ? 2 : 3>(a, src, dst);
     }
 }
 

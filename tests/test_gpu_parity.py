@@ -268,15 +268,16 @@ def test_unstable_state_is_reported():
 
 
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f32s", 1e-5), ("f16s", 1e-3), ("bf16s", 6e-3)])
-def test_two_node_kernel_matches_one_node_kernel(oracle_mod, storage, tol):
-    """The two-nodes-per-thread kernel (packed FP32x2 arithmetic) and the one-node
-    kernel agree with the oracle and with each other (channel walls, force field)."""
+def test_kernel_variants_agree(oracle_mod, storage, tol):
+    """The row-staged kernel (auto), the two-nodes-per-thread kernel (packed FP32x2
+    arithmetic) and the one-node kernel agree with the oracle and with each other
+    (channel walls, force field)."""
     from paper_2107_14774_gb300 import Lattice
     n, r, s = (64, 20, 12), 0.5, 1.0
     rho, u = synth.solenoidal_random(*n, r, s, 3.0, 0.03, seed=21)
     ff = synth.force_field(*n, 1e-5, seed=22)
     out = {}
-    for kern in ("auto", "one"):
+    for kern in ("auto", "pair", "one"):
         lat = Lattice(*n, r_y=r, r_z=s, nu=0.01, storage=storage, walls="y", force=(1e-6, 0, 0), kernel=kern)
         lat.set_force_field(torch.from_numpy(ff).cuda())
         lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(8)
@@ -286,5 +287,6 @@ def test_two_node_kernel_matches_one_node_kernel(oracle_mod, storage, tol):
     o = oracle_mod.Oracle(*n, r=r, s=s, cs2=p["cs2"], omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
                           walls="y", force=(1e-6, 0, 0), force_field=ff)
     _, ur = o.moments(o.run(o.init(rho, u), 8))
-    assert rel(out["auto"], ur) < tol and rel(out["one"], ur) < tol
-    assert rel(out["auto"], out["one"]) < tol
+    for kern in out:
+        assert rel(out[kern], ur) < tol, kern
+    assert rel(out["auto"], out["one"]) < tol and rel(out["pair"], out["one"]) < tol
