@@ -212,6 +212,11 @@ k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
         }
         const char *stage = smem + s * G::stage;
         const unsigned rowoff = (unsigned)r * nx;
+        // rows that came across a y or z wall hold the opposite direction at the node itself
+        int ys[3], zs[3];
+        bool yo[3], zo[3];
+        axis_sources((int)(r % g.ny), g.ny, g.wall[1], ys, yo);
+        axis_sources((int)(r / g.ny), g.nz, g.wall[2], zs, zo);
         for (unsigned i0 = 2 * tid; i0 < nx; i0 += 2 * 32 * kBulkConsumerWarps) {
             const unsigned xm = (i0 == 0) ? nx - 1u : i0 - 1u;       // source of ex = +1 for node i0
             const unsigned xp = (i0 + 2 == nx) ? 0u : i0 + 2u;       // source of ex = -1 for node i0+1
@@ -219,7 +224,7 @@ k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const char *row = stage + a * G::row;
-                if (ex(a) == 0)
+                if (ex(a) == 0 || (yo[ey(a) + 1] | zo[ez(a) + 1]))
                     h[a] = BI::ld2a(row, i0, D.w[a], D.iscale[a]);
                 else if (ex(a) == 1)
                     h[a] = BI::ld2(row, xm, i0, D.w[a], D.iscale[a]);

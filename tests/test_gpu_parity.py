@@ -267,8 +267,9 @@ def test_unstable_state_is_reported():
     lat.close()
 
 
+@pytest.mark.parametrize("walls", ["y", "z", "yz", ""])
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f32s", 1e-5), ("f16s", 1e-3), ("bf16s", 6e-3)])
-def test_kernel_variants_agree(oracle_mod, storage, tol):
+def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
     """The row-staged kernel (auto), the two-nodes-per-thread kernel (packed FP32x2
     arithmetic) and the one-node kernel agree with the oracle and with each other
     (channel walls, force field)."""
@@ -278,14 +279,14 @@ def test_kernel_variants_agree(oracle_mod, storage, tol):
     ff = synth.force_field(*n, 1e-5, seed=22)
     out = {}
     for kern in ("auto", "pair", "one"):
-        lat = Lattice(*n, r_y=r, r_z=s, nu=0.01, storage=storage, walls="y", force=(1e-6, 0, 0), kernel=kern)
+        lat = Lattice(*n, r_y=r, r_z=s, nu=0.01, storage=storage, walls=walls, force=(1e-6, 0, 0), kernel=kern)
         lat.set_force_field(torch.from_numpy(ff).cuda())
         lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(8)
         out[kern] = lat.moments()[1].cpu().numpy()
         p = lat.params
         lat.close()
     o = oracle_mod.Oracle(*n, r=r, s=s, cs2=p["cs2"], omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
-                          walls="y", force=(1e-6, 0, 0), force_field=ff)
+                          walls=walls, force=(1e-6, 0, 0), force_field=ff)
     _, ur = o.moments(o.run(o.init(rho, u), 8))
     for kern in out:
         assert rel(out[kern], ur) < tol, kern
