@@ -275,7 +275,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default=",".join(VARIANTS),
                     help="storage forms to time (comma list of f32,f32s,bf16s,f16s,f64)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged"],
                     help="kernel selection passed to the library (auto = row-staged where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")

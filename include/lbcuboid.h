@@ -96,9 +96,10 @@ typedef struct {
     double lid_u;          /* velocity along x of the wall at j = ny - 1/2 (needs LB_WALL_Y);
                               momentum-augmented bounce-back (Sec. 4, Eq. 69); 0 = at rest */
     void *stream;          /* cudaStream_t to issue all work on; NULL = the legacy default stream */
-    int kernel;            /* 0: automatic (row-staged kernel or two nodes per thread where the
-                              lattice allows it); 1: one node per thread; 2: two nodes per
-                              thread without staging (cross-checks and measurements) */
+    int kernel;            /* 0: automatic (row-staged kernel for 4-byte storage, two nodes per
+                              thread for 2-byte storage, where the lattice allows it); 1: one
+                              node per thread; 2: two nodes per thread without staging;
+                              3: row-staged for every storage form (cross-checks, measurements) */
 } lb_config;
 
 /* Fill *cfg with defaults: FP32 storage, LOCAL corrections, periodic, no

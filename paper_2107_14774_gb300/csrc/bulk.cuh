@@ -1,7 +1,8 @@
-// bulk.cuh -- persistent, warp-specialised variant of the fused step: a producer
-// warp streams the 27 source rows of each lattice row into shared memory with
-// bulk asynchronous copies (cp.async.bulk + mbarrier transaction counts), while
-// the consumer warps collide from shared memory and store to global memory.
+// bulk.cuh -- persistent, row-staged variant of the fused step: the 27 source
+// rows of each lattice row are streamed into shared memory with bulk
+// asynchronous copies (cp.async.bulk + mbarrier transaction counts) several rows
+// ahead, while all warps of the CTA collide from shared memory and store to
+// global memory.
 //
 // Row-wise staging fits the pull layout exactly: for an x-row (j, k) of the
 // destination, direction a needs the whole source row (j - e_ay, k - e_az) of
@@ -12,8 +13,8 @@
 // loads in flight.
 //
 // Every mbarrier wait is bounded: after kSpinLimit polls the thread records an
-// error code in *err and leaves (the producer first waits, again bounded, for
-// the copies it has issued), so a lost arrival can never hang the GPU.
+// error code in *err and leaves (the issuing thread first waits, again bounded,
+// for the copies it has issued), so a lost arrival can never hang the GPU.
 #pragma once
 
 #include <stdint.h>
@@ -22,9 +23,8 @@
 
 namespace lbc {
 
-constexpr int kBulkConsumerWarps = 8;
-constexpr int kBulkThreads = 32 * (kBulkConsumerWarps + 1);
-constexpr unsigned kSpinLimit = 1u << 24;
+constexpr int kBulkThreads = 256;
+constexpr unsigned kSpinLimit = 1u << 22;
 
 enum : int { kErrNone = 0, kErrFullWait = 1, kErrEmptyWait = 2 };
 
@@ -63,10 +63,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 }
 
 // Bounded wait for the phase with the given parity; false if the limit ran out.
+// Repeated polls back off with a short sleep so that waiting warps leave the
+// issue slots to the warps that are computing.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
 {
-    for (unsigned it = 0; it < kSpinLimit; ++it)
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (it >= 2) __nanosleep(64);
+    }
     return false;
 }
 
@@ -141,75 +145,70 @@ struct BulkGeom {
     static constexpr unsigned stage = Q * row;
 };
 
-// Shared memory: NS stages of 27 rows, then 2 NS mbarriers (full, empty).
-template <int ST, int CORR, int NXMAX, int NS>
-__global__ void __launch_bounds__(kBulkThreads, 1)
+// Issue the 27 row copies of lattice row r into one stage (called by one thread).
+template <int ST, int NXMAX>
+__device__ __forceinline__ void bulk_issue_row(const DirPtrs<typename Codec<ST>::S> &ptr, const Geom &g, long long r,
+                                               char *stage, uint64_t *full, unsigned rowbytes)
+{
+    using G = BulkGeom<ST, NXMAX>;
+    const unsigned nx = (unsigned)g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    int ys[3], zs[3];
+    bool yo[3], zo[3];
+    axis_sources(j, g.ny, g.wall[1], ys, yo);
+    axis_sources(k, g.nz, g.wall[2], zs, zo);
+    mbar_arrive_expect_tx(full, Q * rowbytes);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int cy = ey(a) + 1, cz = ez(a) + 1;
+        const typename Codec<ST>::S *src;
+        if (yo[cy] | zo[cz])   // half-way bounce-back: row (j, k) of the opposite direction
+            src = ptr.src[opp(a)] + ((long long)k * g.ny + j) * nx;
+        else
+            src = ptr.src[a] + ((long long)zs[cz] * g.ny + ys[cy]) * nx;
+        bulk_g2s(stage + a * G::row, src, rowbytes, full);
+    }
+}
+
+// Shared memory: NS stages of 27 rows, NS mbarriers (data arrived) and NS
+// counters of the warps that have finished with a stage.  All kBulkThreads threads
+// collide; the last warp to finish with a stage refills it with the row NS ahead,
+// so no warp ever waits for another one.
+template <int ST, int CORR, int NXMAX, int NS, int MINB>
+__global__ void __launch_bounds__(kBulkThreads, MINB)
 k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
             float F2s, const float *__restrict__ ff, int *__restrict__ err)
 {
     using G = BulkGeom<ST, NXMAX>;
     using IO = PairIO<ST>;
     using BI = BulkIO<ST>;
+    constexpr int kWarps = kBulkThreads / 32;
     extern __shared__ __align__(128) char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + NS * G::stage);
-    uint64_t *empty = full + NS;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned *done = reinterpret_cast<unsigned *>(full + NS);
+    const unsigned tid = threadIdx.x, lane = tid & 31;
     const unsigned nx = (unsigned)g.nx;
     const long long nrows = (long long)g.ny * g.nz;
     const unsigned rowbytes = nx * G::elem;
-    if (threadIdx.x == 0) {
+    // rows of this CTA: r(n) = blockIdx.x + n gridDim.x, n = 0 .. nmine - 1
+    const long long nmine = (nrows - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kBulkConsumerWarps);
+            done[s] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (long long m = 0; m < NS && m < nmine; ++m)
+            bulk_issue_row<ST, NXMAX>(ptr, g, blockIdx.x + m * gridDim.x, smem + m * G::stage, &full[m], rowbytes);
     }
     __syncthreads();
-
-    if (warp == kBulkConsumerWarps) {
-        // ---------------- producer ----------------
-        if (lane != 0) return;
-        long long n = 0;
-        for (long long r = blockIdx.x; r < nrows; r += gridDim.x, ++n) {
-            const int s = (int)(n % NS);
-            if (n >= NS && !mbar_wait_bounded(&empty[s], (unsigned)(((n / NS) - 1) & 1))) {
-                atomicExch(err, kErrEmptyWait);
-                break;
-            }
-            const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-            int ys[3], zs[3];
-            bool yo[3], zo[3];
-            axis_sources(j, g.ny, g.wall[1], ys, yo);
-            axis_sources(k, g.nz, g.wall[2], zs, zo);
-            mbar_arrive_expect_tx(&full[s], Q * rowbytes);
-            char *stage = smem + s * G::stage;
-#pragma unroll
-            for (int a = 0; a < Q; ++a) {
-                const int cy = ey(a) + 1, cz = ez(a) + 1;
-                const typename Codec<ST>::S *src;
-                if (yo[cy] | zo[cz])   // half-way bounce-back: row (j, k) of the opposite direction
-                    src = ptr.src[opp(a)] + ((long long)k * g.ny + j) * nx;
-                else
-                    src = ptr.src[a] + ((long long)zs[cz] * g.ny + ys[cy]) * nx;
-                bulk_g2s(stage + a * G::row, src, rowbytes, &full[s]);
-            }
-        }
-        // before leaving, let the copies issued for the last stages land (bounded)
-        const long long issued = n;
-        for (long long m = (issued > NS ? issued - NS : 0); m < issued; ++m)
-            if (!mbar_wait_bounded(&full[m % NS], (unsigned)((m / NS) & 1))) break;
-        return;
-    }
-
-    // ---------------- consumers ----------------
-    const unsigned tid = threadIdx.x;   // 0 .. 32 * kBulkConsumerWarps - 1
-    long long n = 0;
-    for (long long r = blockIdx.x; r < nrows; r += gridDim.x, ++n) {
+    for (long long n = 0; n < nmine; ++n) {
         const int s = (int)(n % NS);
         if (!mbar_wait_bounded(&full[s], (unsigned)((n / NS) & 1))) {
             atomicExch(err, kErrFullWait);
-            return;
+            return;   // every issued copy completes this barrier before any later one can be issued
         }
+        const long long r = blockIdx.x + n * gridDim.x;
         const char *stage = smem + s * G::stage;
         const unsigned rowoff = (unsigned)r * nx;
         // rows that came across a y or z wall hold the opposite direction at the node itself
@@ -217,7 +216,7 @@ k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
         bool yo[3], zo[3];
         axis_sources((int)(r % g.ny), g.ny, g.wall[1], ys, yo);
         axis_sources((int)(r / g.ny), g.nz, g.wall[2], zs, zo);
-        for (unsigned i0 = 2 * tid; i0 < nx; i0 += 2 * 32 * kBulkConsumerWarps) {
+        for (unsigned i0 = 2 * tid; i0 < nx; i0 += 2 * kBulkThreads) {
             const unsigned xm = (i0 == 0) ? nx - 1u : i0 - 1u;       // source of ex = +1 for node i0
             const unsigned xp = (i0 + 2 == nx) ? 0u : i0 + 2u;       // source of ex = -1 for node i0+1
             F2 h[Q];
@@ -243,7 +242,15 @@ k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
                                Fz);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        // done[s] only grows (kWarps divides 2^32): the warp that completes a multiple
+        // of kWarps is the last one off this stage and refills it with row n + NS
+        if (lane == 0 && (atomicAdd(&done[s], 1u) + 1u) % kWarps == 0) {
+            const long long m = n + NS;
+            if (m < nmine) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bulk_issue_row<ST, NXMAX>(ptr, g, blockIdx.x + m * gridDim.x, smem + s * G::stage, &full[s], rowbytes);
+            }
+        }
     }
 }
 

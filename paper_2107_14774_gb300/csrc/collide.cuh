@@ -295,29 +295,26 @@ __device__ __forceinline__ void back_transform_to(Out &&out, const PostState<V> 
     const AxisCols<V> Y = axis_cols(o.uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]);
     const AxisCols<V> Z = axis_cols(o.uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2]);
 
-    // z stage of M^-1 on the sparse non-equilibrium central moments
-    V A00[3], A10[3], A01[3], A11[3], A20[3], A02[3];
-#pragma unroll
-    for (int z = 0; z < 3; ++z) {
-        A00[z] = fma_(o.hFz, Z.g1[z], o.d002 * Z.g2[z]);
-        A10[z] = fma_(o.hFx, Z.g0[z], o.t101 * Z.g1[z]);
-        A01[z] = fma_(o.hFy, Z.g0[z], o.t011 * Z.g1[z]);
-        A11[z] = o.t110 * Z.g0[z];
-        A20[z] = o.d200 * Z.g0[z];
-        A02[z] = o.d020 * Z.g0[z];
-    }
     // rho phi_x phi_y phi_z - w_x w_y w_z = (dr phi_x + dphi_x) P_yz + w_x D_yz with
     // P_yz = phi_y phi_z and D_yz = phi_y phi_z - w_y w_z = dphi_y phi_z + w_y dphi_z
     V ax[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) ax[x] = fma_(o.dr, X.phi[x], X.dphi[x]);
+    // z outermost keeps only one z-slice of the intermediate arrays alive
 #pragma unroll
-    for (int y = 0; y < 3; ++y)
+    for (int z = 0; z < 3; ++z) {
+        // z stage of M^-1 on the sparse non-equilibrium central moments
+        const V A00 = fma_(o.hFz, Z.g1[z], o.d002 * Z.g2[z]);
+        const V A10 = fma_(o.hFx, Z.g0[z], o.t101 * Z.g1[z]);
+        const V A01 = fma_(o.hFy, Z.g0[z], o.t011 * Z.g1[z]);
+        const V A11 = o.t110 * Z.g0[z];
+        const V A20 = o.d200 * Z.g0[z];
+        const V A02 = o.d020 * Z.g0[z];
 #pragma unroll
-        for (int z = 0; z < 3; ++z) {
-            const V B0 = fma_(A00[z], Y.g0[y], fma_(A01[z], Y.g1[y], A02[z] * Y.g2[y]));
-            const V B1 = fma_(A10[z], Y.g0[y], A11[z] * Y.g1[y]);
-            const V B2 = A20[z] * Y.g0[y];
+        for (int y = 0; y < 3; ++y) {
+            const V B0 = fma_(A00, Y.g0[y], fma_(A01, Y.g1[y], A02 * Y.g2[y]));
+            const V B1 = fma_(A10, Y.g0[y], A11 * Y.g1[y]);
+            const V B2 = A20 * Y.g0[y];
             const V Pyz = Y.phi[y] * Z.phi[z];
             const V Dyz = fma_(Y.dphi[y], Z.phi[z], Y.w[y] * Z.dphi[z]);
 #pragma unroll
@@ -326,6 +323,7 @@ __device__ __forceinline__ void back_transform_to(Out &&out, const PostState<V> 
                 out(dir_of(x - 1, y - 1, z - 1), fma_(B0, X.g0[x], fma_(B1, X.g1[x], fma_(B2, X.g2[x], heq))));
             }
         }
+    }
 }
 
 template <class V, class T>

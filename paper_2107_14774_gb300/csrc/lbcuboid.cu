@@ -192,7 +192,7 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (cfg->storage < LB_F64 || cfg->storage > LB_BF16_SHIFTED) return fail(LB_EINVAL, "lb_create_ex: bad storage");
     if (cfg->corr < LB_CORR_NONE || cfg->corr > LB_CORR_FULL) return fail(LB_EINVAL, "lb_create_ex: bad corr");
     if (cfg->wall_mask & ~7u) return fail(LB_EINVAL, "lb_create_ex: bad wall_mask");
-    if (cfg->kernel < 0 || cfg->kernel > 2) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
+    if (cfg->kernel < 0 || cfg->kernel > 3) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
     if (cfg->lid_u != 0.0 && !(cfg->wall_mask & LB_WALL_Y))
         return fail(LB_EINVAL, "lb_create_ex: a moving lid needs walls normal to y");
     const double r = cfg->r_y, s = cfg->r_z;

@@ -25,13 +25,13 @@ struct LaunchArgs {
     cudaStream_t stream;
     const void *force_field;  // device, compute type, [3][N] or null
     void *rho_field;          // device, compute type, [N] (FULL) or null
-    int kernel;               // 0 automatic, 1 one node per thread, 2 two nodes per thread
+    int kernel;               // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 row-staged
     int *err;                 // device error word of the bounded waits (bulk kernel)
     int sm_count;             // multiprocessors of the device
 };
 
 #ifndef LBC_PAIR_PLANES
-#define LBC_PAIR_PLANES 8
+#define LBC_PAIR_PLANES 1
 #endif
 // z-planes per thread of the two-node kernel (software pipelining depth).
 constexpr int kPairPlanes = LBC_PAIR_PLANES;
@@ -131,7 +131,7 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
 template <int ST>
 bool Ops<ST>::use_pair(const LaunchArgs &a)
 {
-    if (ST == LB_F64 || a.kernel == 1) return false;
+    if (ST == LB_F64 || a.kernel == 1) return false;   // (kernel 3 falls back here where staging does not apply)
     return (a.g.nx % 2 == 0) && !a.g.wall[0] && a.lid_u == 0.0 && a.corr != LB_CORR_FULL &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
@@ -172,24 +172,26 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
     }
 }
 
-// The staged (bulk-copy) kernel: FP32-arithmetic storage, LOCAL corrections,
-// rows of at most 1024 elements whose byte length is a multiple of 16, no walls
-// normal to x, no moving lid.
+// The staged (bulk-copy) kernel: 4-byte storage (for the 2-byte forms the
+// two-node kernel from global memory measured faster), LOCAL corrections, rows of
+// at most 1024 elements whose byte length is a multiple of 16, no walls normal to
+// x, no moving lid.
 template <int ST>
 bool Ops<ST>::use_bulk(const LaunchArgs &a)
 {
-    if (ST == LB_F64 || a.kernel != 0 || a.corr != LB_CORR_LOCAL || !a.err) return false;
+    if (ST == LB_F64 || a.corr != LB_CORR_LOCAL || !a.err) return false;
+    if (a.kernel != 3 && (a.kernel != 0 || sizeof(S) != 4)) return false;
     const unsigned elem = (unsigned)sizeof(S);
     return a.g.nx >= 2 && a.g.nx <= 1024 && (a.g.nx * elem) % 16 == 0 && !a.g.wall[0] && a.lid_u == 0.0 &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
 
-template <int ST, int NXMAX, int NS>
+template <int ST, int NXMAX, int NS, int MINB>
 cudaError_t launch_bulk(const LaunchArgs &a, const void *src, void *dst)
 {
     using S = typename Codec<ST>::S;
-    constexpr size_t smem = (size_t)NS * BulkGeom<ST, NXMAX>::stage + 2 * NS * sizeof(uint64_t);
-    auto kern = k_step_bulk<ST, LB_CORR_LOCAL, NXMAX, NS>;
+    constexpr size_t smem = (size_t)NS * BulkGeom<ST, NXMAX>::stage + NS * (sizeof(uint64_t) + sizeof(unsigned));
+    auto kern = k_step_bulk<ST, LB_CORR_LOCAL, NXMAX, NS, MINB>;
     static bool configured = false;   // per instantiation; the attribute is per device function
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -209,21 +211,25 @@ cudaError_t launch_bulk(const LaunchArgs &a, const void *src, void *dst)
         D.iscale[q] = 1.0f / a.scale[q];
     }
     const long long rows = (long long)a.g.ny * a.g.nz;
-    const int grid = (int)std::min<long long>(rows, (long long)a.sm_count);
+    const int grid = (int)std::min<long long>(rows, (long long)a.sm_count * MINB);
     kern<<<grid, kBulkThreads, smem, a.stream>>>(ptr, a.g, P, D, (float)a.F[0], (float)a.F[1], (float)a.F[2],
                                                  static_cast<const float *>(a.force_field), a.err);
     return cudaGetLastError();
 }
 
+// Stage depth and CTAs per multiprocessor: two CTAs of 256 threads per SM
+// (<= 128 registers per thread) whenever two sets of stages fit in shared memory.
 template <int ST>
 cudaError_t Ops<ST>::step_bulk(const LaunchArgs &a, const void *src, void *dst)
 {
     if constexpr (ST == LB_F64) {
         return cudaErrorInvalidValue;
+    } else if constexpr (sizeof(S) == 4) {
+        if (a.g.nx <= 512) return launch_bulk<ST, 512, 2, 2>(a, src, dst);
+        return launch_bulk<ST, 1024, 2, 1>(a, src, dst);
     } else {
-        constexpr bool wide = sizeof(S) == 4;
-        if (a.g.nx <= 512) return launch_bulk<ST, 512, wide ? 3 : 4>(a, src, dst);
-        return launch_bulk<ST, 1024, wide ? 2 : 3>(a, src, dst);
+        if (a.g.nx <= 512) return launch_bulk<ST, 512, 4, 2>(a, src, dst);
+        return launch_bulk<ST, 1024, 2, 2>(a, src, dst);
     }
 }
 

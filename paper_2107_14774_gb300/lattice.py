@@ -36,8 +36,8 @@ class Lattice:
     storage: "f64", "f32", "f32s" (shifted FP32), "f16s", "bf16s" (shifted FP16 /
     BF16, FP32 arithmetic).  corr: "none", "lowmach", "local", "full".
     walls: any of "x", "y", "z" (half-way bounce-back walls normal to that axis).
-    kernel: "auto" (row-staged or two-node kernel where possible), "one" (one node per thread)
-    or "pair" (two nodes per thread, no staging).
+    kernel: "auto" (row-staged or two-node kernel where possible), "one" (one node per thread),
+    "pair" (two nodes per thread, no staging) or "staged" (row-staged for every storage form).
     """
 
     def __init__(self, nx, ny, nz, r_y=1.0, r_z=1.0, nu=0.01, zeta=0.0, cs2=0.0, storage="f32",
@@ -56,7 +56,7 @@ class Lattice:
         cfg.force = (ctypes.c_double * 3)(*force)
         cfg.lid_u = lid_u
         cfg.stream = s.cuda_stream
-        cfg.kernel = {"auto": 0, "one": 1, "pair": 2}[kernel]
+        cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3}[kernel]
         self.cfg = cfg
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz

@@ -278,7 +278,7 @@ def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
     rho, u = synth.solenoidal_random(*n, r, s, 3.0, 0.03, seed=21)
     ff = synth.force_field(*n, 1e-5, seed=22)
     out = {}
-    for kern in ("auto", "pair", "one"):
+    for kern in ("auto", "pair", "one", "staged"):
         lat = Lattice(*n, r_y=r, r_z=s, nu=0.01, storage=storage, walls=walls, force=(1e-6, 0, 0), kernel=kern)
         lat.set_force_field(torch.from_numpy(ff).cuda())
         lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(8)
@@ -290,4 +290,5 @@ def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
     _, ur = o.moments(o.run(o.init(rho, u), 8))
     for kern in out:
         assert rel(out[kern], ur) < tol, kern
-    assert rel(out["auto"], out["one"]) < tol and rel(out["pair"], out["one"]) < tol
+    for kern in ("auto", "pair", "staged"):
+        assert rel(out[kern], out["one"]) < tol, kern
