@@ -34,9 +34,17 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "MLUPS and % of HBM roofline, plain FP32 vs reduced-precision storage at stated error"
-WORKLOAD = dict(workload="decaying anisotropic flow 512x256x256, r_y=0.5, r_z=0.5 (periodic)",
-                nx=512, ny=256, nz=256, r_y=0.5, r_z=0.5, cs2=1.0 / 12.0, nu=0.005, omega_xi=1.0,
-                init="seeded solenoidal velocity, spectrum peak k=4, u_rms=0.03, seed 3", corr="local")
+WORKLOADS = {
+    "decaying": dict(workload="decaying anisotropic flow 512x256x256, r_y=0.5, r_z=0.5 (periodic)",
+                     nx=512, ny=256, nz=256, r_y=0.5, r_z=0.5, cs2=1.0 / 12.0, nu=0.005, omega_xi=1.0,
+                     init="seeded solenoidal velocity, spectrum peak k=4, u_rms=0.03, seed 3", corr="local",
+                     walls="", force=(0.0, 0.0, 0.0)),
+    "channel": dict(workload="wall-bounded channel 768x192x384, r_y=0.25, r_z=1 (walls y, periodic x z)",
+                    nx=768, ny=192, nz=384, r_y=0.25, r_z=1.0, cs2=1.0 / 48.0, nu=0.005, omega_xi=1.0,
+                    init="laminar Poiseuille u_max=0.02 plus seeded wall-damped solenoidal perturbation of 5 %, "
+                         "seed 5; F_x = 8 nu u_max / h^2", corr="local", walls="y", force=None),
+}
+WORKLOAD = dict(WORKLOADS["decaying"])
 BYTES_PER_NODE = {"f64": 432, "f32": 216, "f32s": 216, "f16s": 108, "bf16s": 108}
 VARIANTS = ["f32", "f32s", "bf16s", "f16s"]
 
@@ -107,6 +115,10 @@ class ClockSampler:
 
 def make_inputs():
     w = WORKLOAD
+    if w["walls"] == "y":
+        rho, u, fx = synth.channel(w["nx"], w["ny"], w["nz"], w["r_y"], w["r_z"], 0.02, w["nu"], 0.05, seed=5)
+        w["force"] = (fx, 0.0, 0.0)
+        return rho, u
     rho, u = synth.solenoidal_random(w["nx"], w["ny"], w["nz"], w["r_y"], w["r_z"], 4.0, 0.03, seed=3)
     return rho, u
 
@@ -138,7 +150,8 @@ def run_ours(args, rank, world):
     kernel_ms = {}
     for var in variants:
         lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var,
-                      corr=w["corr"], stream=stream, device=dev, kernel=args.kernel)
+                      corr=w["corr"], stream=stream, device=dev, kernel=args.kernel, walls=w["walls"],
+                      force=w["force"])
         with torch.cuda.stream(stream):
             lat.init(rho_t, u_t)
             lat.step(args.warmup)
@@ -172,7 +185,7 @@ def run_ours(args, rank, world):
             results[var]["u_rel_err_vs_f64"] = None
         return results, kernel_ms, run_e2e(args, rho, u, dims, stream, dev, world, barrier), N
     ref = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage="f64", corr=w["corr"],
-                  stream=stream, device=dev)
+                  stream=stream, device=dev, walls=w["walls"], force=w["force"])
     with torch.cuda.stream(stream):
         ref.init(rho_t.double(), u_t.double()).step(err_steps)
     _, u_ref = ref.moments()
@@ -181,7 +194,7 @@ def run_ours(args, rank, world):
     torch.cuda.empty_cache()
     for var in variants:
         lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var, corr=w["corr"],
-                      stream=stream, device=dev)
+                      stream=stream, device=dev, kernel=args.kernel, walls=w["walls"], force=w["force"])
         with torch.cuda.stream(stream):
             lat.init(rho_t, u_t).step(err_steps)
         _, uu = lat.moments()
@@ -214,7 +227,7 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
     lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage="f32", corr=w["corr"],
-                  stream=stream, device=dev)
+                  stream=stream, device=dev, kernel=args.kernel, walls=w["walls"], force=w["force"])
     e2e_steps = max(3, min(args.steps, 20))
     for _ in range(2):
         lat.init(rho_h, u_h).step(1).moments(rho_o, u_o)
@@ -244,7 +257,7 @@ def oracle_sample(seconds_target=15.0, cores=None):
     wn = 1.0 / (w["nu"] / w["cs2"] + 0.5)
     nzs = 8
     o = oracle.Oracle(w["nx"], w["ny"], nzs, r=w["r_y"], s=w["r_z"], cs2=w["cs2"], omega_nu=wn, omega_xi=1.0,
-                      corr=oracle.CORR_LOCAL, threads=cores or 0)
+                      corr=oracle.CORR_LOCAL, threads=cores or 0, walls=w["walls"], force=w["force"])
     f = o.init(rho[:nzs], u[:, :nzs])
     n = w["nx"] * w["ny"] * nzs
     t0 = time.perf_counter()
@@ -260,7 +273,7 @@ def oracle_sample(seconds_target=15.0, cores=None):
         dt += time.perf_counter() - t0
         steps += extra
     return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": o.threads, "kind": "oracle",
-            "sample": f"{steps} steps of a {w['nx']}x{w['ny']}x{nzs} periodic z-slab of the workload "
+            "sample": f"{steps} steps of a {w['nx']}x{w['ny']}x{nzs} z-slab (periodic in z) of the workload "
                       f"(FP64 C oracle, factored form, OpenMP), {dt:.1f} s"}
 
 
@@ -275,6 +288,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default=",".join(VARIANTS),
                     help="storage forms to time (comma list of f32,f32s,bf16s,f16s,f64)")
+    ap.add_argument("--workload", default="decaying", choices=sorted(WORKLOADS),
+                    help="decaying: 512x256x256 periodic (default); channel: 768x192x384 with y walls")
     ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged"],
                     help="kernel selection passed to the library (auto = row-staged where possible)")
     ap.add_argument("--dims", default=None,
@@ -282,11 +297,12 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     if args.dims:
         nx, ny, nz = (int(v) for v in args.dims.split(","))
-        WORKLOAD.update(nx=nx, ny=ny, nz=nz,
-                        workload=f"decaying anisotropic flow {nx}x{ny}x{nz}, r_y=0.5, r_z=0.5 (periodic)")
-    config = {k: WORKLOAD[k] for k in ("workload", "r_y", "r_z", "cs2", "nu", "omega_xi", "init", "corr")}
+        WORKLOAD.update(nx=nx, ny=ny, nz=nz, workload=WORKLOAD["workload"].split(" ")[0] + f" {nx}x{ny}x{nz} (reduced)")
+    config = {k: WORKLOAD[k] for k in ("workload", "r_y", "r_z", "cs2", "nu", "omega_xi", "init", "corr", "walls")}
     config.update(nodes=WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"], parallelism=f"replicas x{world}",
                   l2="working set (2 x 27 x N stored values) >> 129 MB L2; no flush needed")
 
