@@ -216,6 +216,11 @@ lb_status lb_collide_vjp(lb_ctx *ctx, long long n, const void *f, const void *F,
 lb_status lb_reduce_populations_noalloc(const void *f, int real_size, long long n, double r_y, double r_z,
                                         const double force[3], double out[4], void *stream);
 
+/* Name (with template arguments) of the step kernel lb_step launches for this
+ * context, e.g. "k_step_bulk<F32,LOCAL,512,2,2>"; thread-local storage, valid
+ * until the next call on the same thread. */
+const char *lb_step_kernel(const lb_ctx *ctx);
+
 /* Message of the last error on this thread ("" if none). */
 const char *lb_last_error(void);
 

@@ -70,6 +70,7 @@ SIGNATURES = {
     "lb_reduce_populations_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong, ctypes.c_double,
                                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                                       ctypes.POINTER(ctypes.c_double), _P]),
+    "lb_step_kernel": (ctypes.c_char_p, [_CTX]),
     "lb_last_error": (ctypes.c_char_p, []),
 }
 

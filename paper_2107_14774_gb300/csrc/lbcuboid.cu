@@ -589,6 +589,19 @@ lb_status lb_collide_vjp(lb_ctx *c, long long n, const void *f, const void *F, c
     return sum_pairs(c, wpart, nb, w_bar);
 }
 
+const char *lb_step_kernel(const lb_ctx *c)
+{
+    if (!c) return "";
+    const LaunchArgs a = launch_args(c);
+    switch (c->cfg.storage) {
+    case LB_F64: return Ops<LB_F64>::step_kernel_name(a);
+    case LB_F32: return Ops<LB_F32>::step_kernel_name(a);
+    case LB_F32_SHIFTED: return Ops<LB_F32_SHIFTED>::step_kernel_name(a);
+    case LB_F16_SHIFTED: return Ops<LB_F16_SHIFTED>::step_kernel_name(a);
+    default: return Ops<LB_BF16_SHIFTED>::step_kernel_name(a);
+    }
+}
+
 const char *lb_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

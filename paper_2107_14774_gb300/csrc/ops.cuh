@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 
 #include "kernels.cuh"
 #include "adjoint.cuh"
@@ -68,6 +69,7 @@ struct Ops {
     static cudaError_t step_pair(const LaunchArgs &a, const void *src, void *dst);
     static bool use_bulk(const LaunchArgs &a);
     static cudaError_t step_bulk(const LaunchArgs &a, const void *src, void *dst);
+    static const char *step_kernel_name(const LaunchArgs &a);
     static cudaError_t gather(const LaunchArgs &a, const void *src, void *rho, void *u, void *f);
     static cudaError_t scatter(const LaunchArgs &a, void *dst, const void *rho, const void *u, const void *f);
     static cudaError_t reduce_partial(const LaunchArgs &a, const void *src, double *partial, int nblocks,
@@ -333,6 +335,48 @@ cudaError_t Ops<ST>::collide_vjp(const LaunchArgs &a, const void *f, const void 
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Name of the kernel that step() launches for these arguments (the same
+// decision as step(), spelled with the template arguments).
+inline const char *storage_name(int st)
+{
+    switch (st) {
+    case LB_F64: return "F64";
+    case LB_F32: return "F32";
+    case LB_F32_SHIFTED: return "F32_SHIFTED";
+    case LB_F16_SHIFTED: return "F16_SHIFTED";
+    default: return "BF16_SHIFTED";
+    }
+}
+
+inline const char *corr_name(int c)
+{
+    switch (c) {
+    case LB_CORR_NONE: return "NONE";
+    case LB_CORR_LOWMACH: return "LOWMACH";
+    case LB_CORR_LOCAL: return "LOCAL";
+    default: return "FULL";
+    }
+}
+
+template <int ST>
+const char *Ops<ST>::step_kernel_name(const LaunchArgs &a)
+{
+    static thread_local char buf[96];
+    if (use_bulk(a)) {
+        const bool wide = sizeof(S) == 4, small = a.g.nx <= 512;
+        const int nxmax = small ? 512 : 1024;
+        const int ns = wide ? 2 : (small ? 4 : 2);
+        const int minb = (wide && !small) ? 1 : 2;
+        snprintf(buf, sizeof(buf), "k_step_bulk<%s,%s,%d,%d,%d>", storage_name(ST), corr_name(a.corr), nxmax, ns,
+                 minb);
+    } else if (use_pair(a)) {
+        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s,%d>", storage_name(ST), corr_name(a.corr), kPairPlanes);
+    } else {
+        snprintf(buf, sizeof(buf), "k_step<%s,%s>", storage_name(ST), corr_name(a.corr));
+    }
+    return buf;
 }
 
 }  // namespace lbc

@@ -92,6 +92,11 @@ class Lattice:
         return {"omega_nu": out[0], "omega_xi": out[1], "cs2": out[2]}
 
     @property
+    def step_kernel(self) -> str:
+        """lb_step_kernel: the step kernel lb_step launches for this lattice."""
+        return self.lib.lb_step_kernel(self.ctx).decode()
+
+    @property
     def time_step(self) -> int:
         return self.lib.lb_time_step(self.ctx)
 
