@@ -45,7 +45,7 @@ WORKLOADS = {
                          "seed 5; F_x = 8 nu u_max / h^2", corr="local", walls="y", force=None),
 }
 WORKLOAD = dict(WORKLOADS["decaying"])
-BYTES_PER_NODE = {"f64": 432, "f32": 216, "f32s": 216, "f16s": 108, "bf16s": 108}
+BYTES_PER_NODE = {"f64": 432, "f32": 216, "f32s": 216, "f16s": 108, "bf16s": 108, "f16s+sr": 108, "bf16s+sr": 108}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu
 # capture of the named kernel on the 512x128x128 case, scaled by the node count
 # (profiles/k_step_bulk_f32_decaying512x128x128.md); only reported while the
@@ -155,9 +155,9 @@ def run_ours(args, rank, world):
     kernel_ms = {}
     kernel_names = {}
     for var in variants:
-        lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var,
+        lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var.split("+")[0],
                       corr=w["corr"], stream=stream, device=dev, kernel=args.kernel, walls=w["walls"],
-                      force=w["force"])
+                      force=w["force"], rounding="stochastic" if var.endswith("+sr") else "nearest")
         with torch.cuda.stream(stream):
             lat.init(rho_t, u_t)
             lat.step(args.warmup)
@@ -185,31 +185,45 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
     barrier()
 
-    # velocity error of each storage form against the FP64 path after the same steps
-    err_steps = args.error_steps
-    if err_steps <= 0:
+    # velocity error of each storage form against the FP64 path after the same steps,
+    # at each checkpoint; an FP64 run from an initial velocity perturbed by 1e-7
+    # (relative, seeded) measures how fast the flow itself separates nearby states
+    checkpoints = sorted({int(v) for v in str(args.error_steps).split(",") if int(v) > 0})
+    if not checkpoints:
         for var in variants:
             results[var]["u_rel_err_vs_f64"] = None
         return results, kernel_ms, run_e2e(args, rho, u, dims, stream, dev, world, barrier), N
-    ref = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage="f64", corr=w["corr"],
-                  stream=stream, device=dev, walls=w["walls"], force=w["force"])
-    with torch.cuda.stream(stream):
-        ref.init(rho_t.double(), u_t.double()).step(err_steps)
-    _, u_ref = ref.moments()
-    ref.close()
-    del ref
-    torch.cuda.empty_cache()
-    for var in variants:
-        lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=var, corr=w["corr"],
-                      stream=stream, device=dev, kernel=args.kernel, walls=w["walls"], force=w["force"])
+
+    def trajectory(storage, u0, kern):
+        lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=storage.split("+")[0],
+                      corr=w["corr"], stream=stream, device=dev, kernel=kern, walls=w["walls"], force=w["force"],
+                      rounding="stochastic" if storage.endswith("+sr") else "nearest")
+        out, done = [], 0
         with torch.cuda.stream(stream):
-            lat.init(rho_t, u_t).step(err_steps)
-        _, uu = lat.moments()
-        results[var]["u_rel_err_vs_f64"] = float(torch.linalg.vector_norm(uu.double() - u_ref)
-                                                 / torch.linalg.vector_norm(u_ref))
+            lat.init(rho_t.to(lat.dtype), u0.to(lat.dtype))
+            for cp in checkpoints:
+                lat.step(cp - done)
+                done = cp
+                out.append(lat.moments()[1].double())
         lat.close()
-        del lat
-    del u_ref
+        return out
+
+    def errors(us, ref):
+        res = {}
+        for cp, a, b in zip(checkpoints, us, ref):
+            ke_a, ke_b = float((a * a).sum()), float((b * b).sum())
+            res[str(cp)] = {"u_rel_l2": float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)),
+                            "u2_mean_rel": abs(ke_a / ke_b - 1.0)}
+        return res
+
+    ref = trajectory("f64", u_t.double(), "auto")
+    gen = torch.Generator(device="cpu").manual_seed(17)
+    pert = u_t.double() * (1.0 + 1e-7 * torch.randn(u_t.shape, generator=gen, dtype=torch.float64).to(dev))
+    control = errors(trajectory("f64", pert, "auto"), ref)
+    for var in variants:
+        results[var]["u_rel_err_vs_f64"] = errors(trajectory(var, u_t, args.kernel), ref)
+    results["_control_f64_perturbed_1e-7"] = control
+    del ref
     torch.cuda.empty_cache()
     return results, kernel_ms, run_e2e(args, rho, u, dims, stream, dev, world, barrier), N
 
@@ -290,11 +304,13 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--error-steps", type=int, default=100)
+    ap.add_argument("--error-steps", default="100",
+                    help="comma list of step counts at which each storage form is compared with the FP64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--variants", default=",".join(VARIANTS),
-                    help="storage forms to time (comma list of f32,f32s,bf16s,f16s,f64)")
+                    help="storage forms to time (comma list of f32,f32s,bf16s,f16s,f64; "
+                         "bf16s+sr / f16s+sr: stochastic rounding)")
     ap.add_argument("--workload", default="decaying", choices=sorted(WORKLOADS),
                     help="decaying: 512x256x256 periodic (default); channel: 768x192x384 with y walls")
     ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged"],
@@ -346,13 +362,14 @@ def main():
             "peak_source": f"{which} hbm_gbs (copy bandwidth)", "kernel": r["kernel"],
             "algorithmic_bytes_per_launch": BYTES_PER_NODE[main_var] * N}
     variants = {}
+    control = results.pop("_control_f64_perturbed_1e-7", None)
     for var in results:
         v = results[var]
         ach = BYTES_PER_NODE[var] * N / (kernel_ms[var] * 1e-3) / 1e9
         variants[var] = {"mlups": round(v["mlups"], 1), "ms_per_step": round(v["ms_per_step"], 4),
                          "bytes_per_node": BYTES_PER_NODE[var], "achieved_gbs": round(ach, 1),
                          "hbm_frac": round(ach / peak, 4), "kernel": v["kernel"],
-                         f"u_rel_err_vs_f64_after_{args.error_steps}_steps": v["u_rel_err_vs_f64"],
+                         "error_vs_f64": v["u_rel_err_vs_f64"],
                          "clocks": v["clocks"]}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -362,7 +379,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_var == "f64" else "f32", "data": "synthetic", "config": config,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "storage": main_var,
-            "clocks": r["clocks"], "variants": variants}
+            "clocks": r["clocks"], "variants": variants,
+            "error_control_f64_perturbed_1e-7": control}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

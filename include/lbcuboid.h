@@ -96,6 +96,10 @@ typedef struct {
     double lid_u;          /* velocity along x of the wall at j = ny - 1/2 (needs LB_WALL_Y);
                               momentum-augmented bounce-back (Sec. 4, Eq. 69); 0 = at rest */
     void *stream;          /* cudaStream_t to issue all work on; NULL = the legacy default stream */
+    int rounding;          /* 16-bit storage only: 0 = round to nearest even, 1 = stochastic
+                              rounding (hardware cvt.rs, random bits from a counter-based hash
+                              of (node, direction, time step, rounding_seed)) */
+    unsigned rounding_seed;
     int kernel;            /* 0: automatic (row-staged kernel for 4-byte storage, two nodes per
                               thread for 2-byte storage, where the lattice allows it); 1: one
                               node per thread; 2: two nodes per thread without staging;
@@ -185,6 +189,7 @@ lb_status lb_objective_ke(lb_ctx *ctx, double *J);
  * the state after the T steps (as after lb_step(ctx, T)).  Corrections NONE,
  * LOWMACH or LOCAL; no moving lid (LB_EINVAL otherwise).  Synchronises. */
 lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2], double *J);
+/* (lb_adjoint_ke also requires round-to-nearest storage: rounding = 0.) */
 
 /* Vector-Jacobian product of the per-node collision alone, for n independent
  * nodes (device pointers, real type): f [27][n] pre-collision populations,

@@ -34,7 +34,7 @@ class lb_config(ctypes.Structure):
         ("nu", ctypes.c_double), ("zeta", ctypes.c_double), ("cs2", ctypes.c_double),
         ("storage", ctypes.c_int), ("corr", ctypes.c_int), ("wall_mask", ctypes.c_uint),
         ("force", ctypes.c_double * 3), ("lid_u", ctypes.c_double), ("stream", ctypes.c_void_p),
-        ("kernel", ctypes.c_int),
+        ("rounding", ctypes.c_int), ("rounding_seed", ctypes.c_uint), ("kernel", ctypes.c_int),
     ]
 
 

@@ -177,7 +177,7 @@ __device__ __forceinline__ void bulk_issue_row(const DirPtrs<typename Codec<ST>:
 template <int ST, int CORR, int NXMAX, int NS, int MINB>
 __global__ void __launch_bounds__(kBulkThreads, MINB)
 k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
-            float F2s, const float *__restrict__ ff, int *__restrict__ err)
+            float F2s, const float *__restrict__ ff, int *__restrict__ err, unsigned sr_key)
 {
     using G = BulkGeom<ST, NXMAX>;
     using IO = PairIO<ST>;
@@ -238,8 +238,15 @@ k_step_bulk(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
                 Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
                 Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
             }
-            collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy,
-                               Fz);
+            unsigned rs = hash32(self * 0x9e3779b1u + sr_key) | 1u;
+            collide_pair<CORR>(h,
+                               [&](int a, F2 v) {
+                                   if (sr_key)
+                                       IO::st2sr(ptr.dst[a] + self, v, D.w[a], D.scale[a], xorshift32(rs));
+                                   else
+                                       IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]);
+                               },
+                               P, Fx, Fy, Fz);
         }
         __syncwarp();
         // done[s] only grows (kWarps divides 2^32): the warp that completes a multiple

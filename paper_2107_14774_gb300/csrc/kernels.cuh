@@ -16,6 +16,41 @@
 
 namespace lbc {
 
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the 16-bit storage forms (optional, lb_config.rounding).
+// Random bits: the lowbias32 integer hash (C. Wellons) of a per-node key, then one
+// xorshift32 step (G. Marsaglia, 2003) per stored value.  The conversion is the
+// hardware stochastic-rounding cvt.rs of sm_100+ (unbiased: E[round(x)] = x).
+__device__ __forceinline__ unsigned hash32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ unsigned xorshift32(unsigned &s)
+{
+    s ^= s << 13;
+    s ^= s >> 17;
+    s ^= s << 5;
+    return s;
+}
+// Packed pair: `lo` goes to the lower 16 bits, `hi` to the upper ones.
+__device__ __forceinline__ unsigned cvt_rs_bf16x2(float lo, float hi, unsigned rbits)
+{
+    unsigned d;
+    asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+__device__ __forceinline__ unsigned cvt_rs_f16x2(float lo, float hi, unsigned rbits)
+{
+    unsigned d;
+    asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
+}
+
 constexpr int kBlockX = 32;   // threads along x per block
 constexpr int kBlockThreads = 128;
 
@@ -139,7 +174,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__restrict__ dst, Geom g,
        Phys<typename Codec<ST>::T> P, DirConst<typename Codec<ST>::T> D, typename Codec<ST>::T F0,
        typename Codec<ST>::T F1, typename Codec<ST>::T F2, const typename Codec<ST>::T *__restrict__ ff,
-       const typename Codec<ST>::T *__restrict__ rho_field, typename Codec<ST>::T lid_u)
+       const typename Codec<ST>::T *__restrict__ rho_field, typename Codec<ST>::T lid_u, unsigned sr_key)
 {
     using C = Codec<ST>;
     using T = typename C::T;
@@ -195,6 +230,19 @@ k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__r
         grz = gr[2];
     }
     collide<T, CORR>(h, P, Fx, Fy, Fz, grx, gry, grz);
+    if (ST == LB_F16_SHIFTED || ST == LB_BF16_SHIFTED) {
+        if (sr_key) {
+            unsigned rs = hash32((unsigned)q.base * 0x9e3779b1u + sr_key) | 1u;
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const unsigned r = xorshift32(rs);
+                const float v = (float)h[a] * D.scale[a];
+                const unsigned packed = (ST == LB_F16_SHIFTED) ? cvt_rs_f16x2(v, 0.f, r) : cvt_rs_bf16x2(v, 0.f, r);
+                reinterpret_cast<unsigned short *>(dst)[(long long)a * N + q.base] = (unsigned short)(packed & 0xffffu);
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int a = 0; a < Q; ++a) dst[(long long)a * N + q.base] = C::store(h[a], D.w[a], D.scale[a]);
 }
@@ -224,6 +272,7 @@ template <> struct PairIO<LB_F32> {
     {
         *reinterpret_cast<float2 *>(p) = (h + F2(w)).v;
     }
+    static __device__ __forceinline__ void st2sr(S *p, F2 h, float w, float s, unsigned) { st2(p, h, w, s); }
 };
 template <> struct PairIO<LB_F32_SHIFTED> {
     using S = float;
@@ -232,6 +281,7 @@ template <> struct PairIO<LB_F32_SHIFTED> {
     static __device__ __forceinline__ Raw ld11(const S *p0, const S *p1) { return make_float2(__ldg(p0), __ldg(p1)); }
     static __device__ __forceinline__ F2 dec(Raw r, float, float) { return F2(r); }
     static __device__ __forceinline__ void st2(S *p, F2 h, float, float) { *reinterpret_cast<float2 *>(p) = h.v; }
+    static __device__ __forceinline__ void st2sr(S *p, F2 h, float w, float s, unsigned) { st2(p, h, w, s); }
 };
 // 16-bit forms: the raw word holds the element at the lower address in its low half.
 __device__ __forceinline__ unsigned ld16x2(const void *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
@@ -256,6 +306,11 @@ template <> struct PairIO<LB_F16_SHIFTED> {
     {
         *reinterpret_cast<__half2 *>(p) = __float22half2_rn((h * F2(scale)).v);
     }
+    static __device__ __forceinline__ void st2sr(S *p, F2 h, float, float scale, unsigned rbits)
+    {
+        const F2 v = h * F2(scale);
+        *reinterpret_cast<unsigned *>(p) = cvt_rs_f16x2(v.v.x, v.v.y, rbits);
+    }
 };
 template <> struct PairIO<LB_BF16_SHIFTED> {
     using S = __nv_bfloat16;
@@ -270,6 +325,10 @@ template <> struct PairIO<LB_BF16_SHIFTED> {
     static __device__ __forceinline__ void st2(S *p, F2 h, float, float)
     {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(h.v);
+    }
+    static __device__ __forceinline__ void st2sr(S *p, F2 h, float, float, unsigned rbits)
+    {
+        *reinterpret_cast<unsigned *>(p) = cvt_rs_bf16x2(h.v.x, h.v.y, rbits);
     }
 };
 
@@ -324,10 +383,10 @@ __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], c
 #ifndef LBC_PAIR_MINBLOCKS
 #define LBC_PAIR_MINBLOCKS 1
 #endif
-template <int ST, int CORR, int ZC>
+template <int ST, int CORR, int ZC, bool SR>
 __global__ void __launch_bounds__(kBlockThreads, LBC_PAIR_MINBLOCKS)
 k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
-            float F2s, const float *__restrict__ ff)
+            float F2s, const float *__restrict__ ff, unsigned sr_key)
 {
     using IO = PairIO<ST>;
     const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -356,7 +415,15 @@ k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
             Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
             Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
         }
-        collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy, Fz);
+        if constexpr (SR) {
+            unsigned rs = hash32(self * 0x9e3779b1u + sr_key) | 1u;
+            collide_pair<CORR>(
+                h, [&](int a, F2 v) { IO::st2sr(ptr.dst[a] + self, v, D.w[a], D.scale[a], xorshift32(rs)); }, P, Fx,
+                Fy, Fz);
+        } else {
+            collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy,
+                               Fz);
+        }
     }
 }
 

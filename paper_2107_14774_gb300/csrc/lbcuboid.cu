@@ -79,6 +79,10 @@ struct lb_ctx {
 
 namespace {
 
+// Key of the stochastic-rounding draws of one time step (0 = round to nearest):
+// the lowbias32 hash (C. Wellons) of the seed mixed with the step index.
+unsigned step_key(const lb_ctx *c);
+
 LaunchArgs launch_args(const lb_ctx *c)
 {
     LaunchArgs a;
@@ -101,7 +105,20 @@ LaunchArgs launch_args(const lb_ctx *c)
     a.kernel = c->cfg.kernel;
     a.err = c->err;
     a.sm_count = c->sm_count;
+    a.sr_key = step_key(c);
     return a;
+}
+
+unsigned step_key(const lb_ctx *c)
+{
+    if (c->cfg.rounding != 1) return 0u;
+    unsigned x = c->cfg.rounding_seed ^ (unsigned)(c->t * 0x9e3779b97f4a7c15ull) ^ (unsigned)((c->t >> 32) * 0x85ebca6bu);
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x | 1u;
 }
 
 template <class F>
@@ -193,6 +210,9 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (cfg->corr < LB_CORR_NONE || cfg->corr > LB_CORR_FULL) return fail(LB_EINVAL, "lb_create_ex: bad corr");
     if (cfg->wall_mask & ~7u) return fail(LB_EINVAL, "lb_create_ex: bad wall_mask");
     if (cfg->kernel < 0 || cfg->kernel > 3) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
+    if (cfg->rounding < 0 || cfg->rounding > 1) return fail(LB_EINVAL, "lb_create_ex: bad rounding mode");
+    if (cfg->rounding == 1 && cfg->storage != LB_F16_SHIFTED && cfg->storage != LB_BF16_SHIFTED)
+        return fail(LB_EINVAL, "lb_create_ex: stochastic rounding applies to FP16/BF16 storage only");
     if (cfg->lid_u != 0.0 && !(cfg->wall_mask & LB_WALL_Y))
         return fail(LB_EINVAL, "lb_create_ex: a moving lid needs walls normal to y");
     const double r = cfg->r_y, s = cfg->r_z;
@@ -506,6 +526,7 @@ lb_status lb_adjoint_ke(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2],
     if (T < 1 || K < 1) return fail(LB_EINVAL, "lb_adjoint_ke: T and K must be >= 1");
     if (c->cfg.corr == LB_CORR_FULL) return fail(LB_EINVAL, "lb_adjoint_ke: corrections FULL are not supported");
     if (c->cfg.lid_u != 0.0) return fail(LB_EINVAL, "lb_adjoint_ke: a moving lid is not supported");
+    if (c->cfg.rounding != 0) return fail(LB_EINVAL, "lb_adjoint_ke: needs round-to-nearest storage");
     if (K > T) K = T;
     const size_t sb = lb_state_bytes(c);
     const long long N = c->g.N;

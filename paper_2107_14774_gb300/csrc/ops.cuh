@@ -29,6 +29,7 @@ struct LaunchArgs {
     int kernel;               // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 row-staged
     int *err;                 // device error word of the bounded waits (bulk kernel)
     int sm_count;             // multiprocessors of the device
+    unsigned sr_key;          // non-zero: stochastic rounding of 16-bit stores with this step key
 };
 
 #ifndef LBC_PAIR_PLANES
@@ -109,19 +110,19 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
     switch (a.corr) {
     case LB_CORR_NONE:
         k_step<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
-                                                                ff, rf, (T)a.lid_u);
+                                                                ff, rf, (T)a.lid_u, a.sr_key);
         break;
     case LB_CORR_LOWMACH:
         k_step<ST, LB_CORR_LOWMACH><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1],
-                                                                   (T)a.F[2], ff, rf, (T)a.lid_u);
+                                                                   (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
         break;
     case LB_CORR_LOCAL:
         k_step<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
-                                                                 ff, rf, (T)a.lid_u);
+                                                                 ff, rf, (T)a.lid_u, a.sr_key);
         break;
     default:
         k_step<ST, LB_CORR_FULL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
-                                                                ff, rf, (T)a.lid_u);
+                                                                ff, rf, (T)a.lid_u, a.sr_key);
         break;
     }
     return cudaGetLastError();
@@ -159,15 +160,31 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
         }
         const float *ff = static_cast<const float *>(a.force_field);
         const float F0 = (float)a.F[0], F1 = (float)a.F[1], F2 = (float)a.F[2];
+        const bool sr = a.sr_key != 0 && sizeof(S) == 2;
         switch (a.corr) {
         case LB_CORR_NONE:
-            k_step_pair<ST, LB_CORR_NONE, ZC><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            if (sr)
+                k_step_pair<ST, LB_CORR_NONE, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                                                                                      a.sr_key);
+            else
+                k_step_pair<ST, LB_CORR_NONE, ZC, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                                                                                       0u);
             break;
         case LB_CORR_LOWMACH:
-            k_step_pair<ST, LB_CORR_LOWMACH, ZC><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            if (sr)
+                k_step_pair<ST, LB_CORR_LOWMACH, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
+                                                                                         ff, a.sr_key);
+            else
+                k_step_pair<ST, LB_CORR_LOWMACH, ZC, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
+                                                                                          ff, 0u);
             break;
         default:
-            k_step_pair<ST, LB_CORR_LOCAL, ZC><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff);
+            if (sr)
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                                                                                       a.sr_key);
+            else
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                                                                                        0u);
             break;
         }
         return cudaGetLastError();
@@ -215,7 +232,7 @@ cudaError_t launch_bulk(const LaunchArgs &a, const void *src, void *dst)
     const long long rows = (long long)a.g.ny * a.g.nz;
     const int grid = (int)std::min<long long>(rows, (long long)a.sm_count * MINB);
     kern<<<grid, kBulkThreads, smem, a.stream>>>(ptr, a.g, P, D, (float)a.F[0], (float)a.F[1], (float)a.F[2],
-                                                 static_cast<const float *>(a.force_field), a.err);
+                                                 static_cast<const float *>(a.force_field), a.err, a.sr_key);
     return cudaGetLastError();
 }
 
@@ -372,7 +389,8 @@ const char *Ops<ST>::step_kernel_name(const LaunchArgs &a)
         snprintf(buf, sizeof(buf), "k_step_bulk<%s,%s,%d,%d,%d>", storage_name(ST), corr_name(a.corr), nxmax, ns,
                  minb);
     } else if (use_pair(a)) {
-        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s,%d>", storage_name(ST), corr_name(a.corr), kPairPlanes);
+        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s,%d,%s>", storage_name(ST), corr_name(a.corr), kPairPlanes,
+                 (a.sr_key != 0 && sizeof(S) == 2) ? "true" : "false");
     } else {
         snprintf(buf, sizeof(buf), "k_step<%s,%s>", storage_name(ST), corr_name(a.corr));
     }

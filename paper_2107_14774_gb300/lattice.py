@@ -38,11 +38,12 @@ class Lattice:
     walls: any of "x", "y", "z" (half-way bounce-back walls normal to that axis).
     kernel: "auto" (row-staged or two-node kernel where possible), "one" (one node per thread),
     "pair" (two nodes per thread, no staging) or "staged" (row-staged for every storage form).
+    rounding: "nearest" or "stochastic" (FP16/BF16 storage only).
     """
 
     def __init__(self, nx, ny, nz, r_y=1.0, r_z=1.0, nu=0.01, zeta=0.0, cs2=0.0, storage="f32",
                  corr="local", walls="", force=(0.0, 0.0, 0.0), lid_u=0.0, stream=None, device=None,
-                 kernel="auto"):
+                 kernel="auto", rounding="nearest", rounding_seed=0):
         self.lib = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
@@ -57,6 +58,8 @@ class Lattice:
         cfg.lid_u = lid_u
         cfg.stream = s.cuda_stream
         cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3}[kernel]
+        cfg.rounding = {"nearest": 0, "stochastic": 1}[rounding]
+        cfg.rounding_seed = rounding_seed
         self.cfg = cfg
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
