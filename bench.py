@@ -118,6 +118,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def allreduce_max(x: float, dev=None) -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one).
+    NCCL reduces a device tensor, gloo a host tensor."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    on_dev = dist.get_backend() == "nccl"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev if on_dev else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(nodes_per_rank: int, steps: int, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: node updates of all ranks over the slowest rank's time."""
+    return nodes_per_rank * steps * world / seconds_max / 1e6
+
+
 def make_inputs():
     w = WORKLOAD
     if w["walls"] == "y":
@@ -141,6 +159,7 @@ def run_ours(args, rank, world):
     rho, u = make_inputs()
     rho_t = torch.from_numpy(rho.astype(np.float32)).to(dev)
     u_t = torch.from_numpy(u.astype(np.float32)).to(dev)
+    torch.cuda.synchronize(dev)
     stream = torch.cuda.Stream(dev)
     dist = None
     if world > 1:
@@ -171,14 +190,10 @@ def run_ours(args, rank, world):
             ev1.record(stream)
             ev1.synchronize()
         torch.cuda.synchronize(dev)
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = allreduce_max(ev0.elapsed_time(ev1), dev)
         kernel_ms[var] = ms / args.steps
         kernel_names[var] = lat.step_kernel
-        results[var] = {"mlups": N * args.steps * world / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+        results[var] = {"mlups": aggregate_mlups(N, args.steps, world, ms * 1e-3), "ms_per_step": ms / args.steps,
                         "clocks": clk.summary(), "kernel": kernel_names[var]}
         lat.close()
         del lat
@@ -195,6 +210,7 @@ def run_ours(args, rank, world):
         return results, kernel_ms, run_e2e(args, rho, u, dims, stream, dev, world, barrier), N
 
     def trajectory(storage, u0, kern):
+        torch.cuda.synchronize(dev)   # inputs were made on the current stream; the lattice uses `stream`
         lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=storage.split("+")[0],
                       corr=w["corr"], stream=stream, device=dev, kernel=kern, walls=w["walls"], force=w["force"],
                       rounding="stochastic" if storage.endswith("+sr") else "nearest")
@@ -257,13 +273,9 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         lat.init(rho_h, u_h).step(1).moments(rho_o, u_o)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = allreduce_max(time.perf_counter() - t0, dev)
     lat.close()
-    e2e = {"value": N * e2e_steps * world / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 16 * N,
+    e2e = {"value": aggregate_mlups(N, e2e_steps, world, e2e_s), "unit": "MLUPS", "h2d_bytes_per_step": 16 * N,
            "d2h_bytes_per_step": 16 * N,
            "what": "lb_init from pinned host rho,u + lb_step(1) + lb_moments to pinned host, per step"}
     return e2e

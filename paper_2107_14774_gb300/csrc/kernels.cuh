@@ -383,8 +383,9 @@ __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], c
 #ifndef LBC_PAIR_MINBLOCKS
 #define LBC_PAIR_MINBLOCKS 1
 #endif
+// (the stochastic-rounding variant keeps 4 CTAs per SM, i.e. <= 128 registers)
 template <int ST, int CORR, int ZC, bool SR>
-__global__ void __launch_bounds__(kBlockThreads, LBC_PAIR_MINBLOCKS)
+__global__ void __launch_bounds__(kBlockThreads, SR ? 4 : LBC_PAIR_MINBLOCKS)
 k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
             float F2s, const float *__restrict__ ff, unsigned sr_key)
 {

@@ -199,7 +199,9 @@ template <int ST>
 bool Ops<ST>::use_bulk(const LaunchArgs &a)
 {
     if (ST == LB_F64 || a.corr != LB_CORR_LOCAL || !a.err) return false;
-    if (a.kernel != 3 && (a.kernel != 0 || sizeof(S) != 4)) return false;
+    // automatic choice: 4-byte storage on rows of at most 512 nodes (two CTAs per SM);
+    // wider rows leave one CTA of 8 warps per SM, where the two-node kernel measured faster
+    if (a.kernel != 3 && (a.kernel != 0 || sizeof(S) != 4 || a.g.nx > 512)) return false;
     const unsigned elem = (unsigned)sizeof(S);
     return a.g.nx >= 2 && a.g.nx <= 1024 && (a.g.nx * elem) % 16 == 0 && !a.g.wall[0] && a.lid_u == 0.0 &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
