@@ -171,6 +171,11 @@ lb_status lb_set_state(lb_ctx *ctx, const void *src, long long time_step);
 /* Number of completed time steps since the last lb_init / lb_set_populations. */
 long long lb_time_step(const lb_ctx *ctx);
 
+/* Replace the uniform body force for the steps enqueued after this call (a
+ * time-dependent forcing such as the pulsatile duct of Sec. 5.2 updates it
+ * between lb_step calls). */
+lb_status lb_set_force(lb_ctx *ctx, const double force[3]);
+
 /* Set the relaxation rates directly, 0 < omega < 2 (instead of nu, zeta). */
 lb_status lb_set_rates(lb_ctx *ctx, double omega_nu, double omega_xi);
 

@@ -129,6 +129,10 @@ class Oracle:
     def threads(self) -> int:
         return self.lib.or_num_threads(0)
 
+    def set_force(self, force):
+        """Uniform body force for the following steps (a time-dependent forcing)."""
+        self.p.force = (ctypes.c_double * 3)(*[float(v) for v in force])
+
     # ---- single node -------------------------------------------------------
     def collide_node(self, f, F=(0.0, 0.0, 0.0), grad_rho=(0.0, 0.0, 0.0)) -> np.ndarray:
         f, F, g = _f64(f), _f64(F), _f64(grad_rho)

@@ -62,6 +62,7 @@ SIGNATURES = {
     "lb_get_state": (ctypes.c_int, [_CTX, _P]),
     "lb_set_state": (ctypes.c_int, [_CTX, _P, ctypes.c_longlong]),
     "lb_time_step": (ctypes.c_longlong, [_CTX]),
+    "lb_set_force": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double)]),
     "lb_set_rates": (ctypes.c_int, [_CTX, ctypes.c_double, ctypes.c_double]),
     "lb_objective_ke": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double)]),
     "lb_adjoint_ke": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double),

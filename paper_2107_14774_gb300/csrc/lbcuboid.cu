@@ -458,6 +458,16 @@ lb_status lb_set_state(lb_ctx *c, const void *src, long long time_step)
     return LB_OK;
 }
 
+lb_status lb_set_force(lb_ctx *c, const double force[3])
+{
+    if (!c || !force) return fail(LB_EINVAL, "lb_set_force: null argument");
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(force[i])) return fail(LB_EINVAL, "lb_set_force: non-finite force");
+        c->cfg.force[i] = force[i];
+    }
+    return LB_OK;
+}
+
 lb_status lb_set_rates(lb_ctx *c, double omega_nu, double omega_xi)
 {
     if (!c) return fail(LB_EINVAL, "lb_set_rates: null context");

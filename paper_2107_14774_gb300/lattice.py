@@ -178,6 +178,11 @@ class Lattice:
         return self
 
     # ------------------------------------------------------------ adjoint
+    def set_force(self, force):
+        """lb_set_force: uniform body force for the following steps."""
+        check(self.lib.lb_set_force(self.ctx, (ctypes.c_double * 3)(*[float(v) for v in force])))
+        return self
+
     def set_rates(self, omega_nu: float, omega_xi: float):
         """lb_set_rates: relaxation rates directly (0 < omega < 2)."""
         check(self.lib.lb_set_rates(self.ctx, float(omega_nu), float(omega_xi)))

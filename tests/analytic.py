@@ -67,3 +67,25 @@ def fit_decay_rate(times, amps):
     A = np.vstack([t, np.ones_like(t)]).T
     slope, _ = np.linalg.lstsq(A, la, rcond=None)[0]
     return -slope
+
+
+def pulsatile_duct(y, z, t, a, Fm, omega, nu, rho=1.0, nterms=200):
+    """Time-periodic flow in the square duct |y|, |z| <= a driven by F = Fm cos(omega t)
+    along x (Sec. 5.2, Eq. pulsatileflowanalyticalsolution): u = Re[U e^{i omega t}],
+    U = Fm/(i omega rho) (1 - V), V = 2 sum_n (-1)^n / p_n [cosh(g_n y/a) cos(p_n z/a)
+    + cosh(g_n z/a) cos(p_n y/a)] / cosh(g_n), p_n = (2n+1) pi / 2,
+    g_n = sqrt(p_n^2 + i Wo^2), Wo = a sqrt(omega / nu).  Readings of the garbled print:
+    the prefactor is Fm/(i omega) (the printed Fm/omega lacks the i that makes the
+    core oscillate as (Fm/omega) sin(omega t)) and 1/p^n is 1/p_n."""
+    y = np.asarray(y, dtype=float)
+    z = np.asarray(z, dtype=float)
+    wo2 = a * a * omega / nu
+    V = np.zeros(np.broadcast(y, z).shape, dtype=complex)
+    for n in range(nterms):
+        p = (2 * n + 1) * np.pi / 2
+        g = np.sqrt(p * p + 1j * wo2)
+        # cosh(g q/a)/cosh(g) written with decaying exponentials (|q| <= a, Re g > 0)
+        ch = lambda q: (np.exp(g * (np.abs(q) / a - 1)) + np.exp(-g * (np.abs(q) / a + 1))) / (1 + np.exp(-2 * g))
+        V += 2 * (-1) ** n / p * (ch(y) * np.cos(p * z / a) + ch(z) * np.cos(p * y / a))
+    U = Fm / (1j * omega * rho) * (1 - V)
+    return np.real(U * np.exp(1j * omega * t))

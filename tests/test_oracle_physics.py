@@ -176,3 +176,72 @@ def test_local_strain_rates_match_velocity_gradients(oracle_mod):
     assert np.abs(rec[0] - dxux).max() < 0.03 * scale
     assert np.abs(rec[2] - dzuz).max() < 0.03 * scale
     assert np.abs(rec[1]).max() < 0.01 * scale
+
+
+def test_pulsatile_series_solves_the_forced_diffusion_problem():
+    """The pulsatile-duct series satisfies du/dt = nu (u_yy + u_zz) + Fm cos(omega t)/rho
+    inside the duct and vanishes on the walls (checked by finite differences)."""
+    from tests.analytic import pulsatile_duct
+    a, Fm, T, nu = 20.0, 1e-5, 10000.0, 0.0263
+    om = 2 * np.pi / T
+    h, dt = 1e-2, 1.0
+    for (y, z, t) in [(3.0, -7.0, 1234.0), (-15.0, 12.0, 8000.0), (0.0, 0.0, 500.0)]:
+        u = lambda yy, zz, tt: pulsatile_duct(yy, zz, tt, a, Fm, om, nu, nterms=400)
+        dudt = (u(y, z, t + dt) - u(y, z, t - dt)) / (2 * dt)
+        lap = (u(y + h, z, t) + u(y - h, z, t) + u(y, z + h, t) + u(y, z - h, t) - 4 * u(y, z, t)) / h ** 2
+        assert dudt == pytest.approx(nu * lap + Fm * np.cos(om * t), rel=5e-3, abs=1e-3 * Fm)
+    for (y, z) in [(a, 3.0), (-a, -11.0), (5.0, a)]:
+        assert abs(pulsatile_duct(y, z, 777.0, a, Fm, om, nu, nterms=400)) < 1e-3 * Fm / om
+
+
+def test_time_dependent_force_in_the_oracle(oracle_mod):
+    """Changing the uniform force between steps: momentum grows by N F(t) per step."""
+    n = (4, 3, 5)
+    o = oracle_mod.Oracle(*n, r=0.5, s=1.0, cs2=0.04, omega_nu=1.2, omega_xi=1.0)
+    f = o.init(np.ones(n[::-1]), np.zeros((3,) + n[::-1]))
+    ec = o.velocities() * np.array([[1.0], [0.5], [1.0]])
+    total = np.zeros(3)
+    for k in range(5):
+        F = np.array([1e-4 * np.cos(0.3 * k), -2e-5 * k, 0.0])
+        o.set_force(F)
+        f = o.step(f)
+        total += F
+    np.testing.assert_allclose(np.einsum("iq,qzyx->i", ec, f), np.prod(n) * total, rtol=1e-10, atol=1e-16)
+
+
+def _pulsatile_errors(oracle_mod, a, r, s, nu, Wo, Fm=1e-5):
+    """Run the pulsatile duct from rest for three periods; relative L2 error of u_x
+    against the series at the four quarter periods of the fourth."""
+    from tests.analytic import pulsatile_duct
+    ny, nz = int(round(2 * a / r)), int(round(2 * a / s))
+    om = Wo * Wo * nu / (a * a)
+    T = 2 * np.pi / om
+    o = _make(oracle_mod, (1, ny, nz), r, s, min(1.0, r * r, s * s) / 3, nu, walls="yz")
+    f = o.init(np.ones((nz, ny, 1)), np.zeros((3, nz, ny, 1)))
+    Z, Y = np.meshgrid((np.arange(nz) + 0.5) * s - a, (np.arange(ny) + 0.5) * r - a, indexing="ij")
+    amp = np.abs(pulsatile_duct(Y, Z, 0.0, a, Fm, om, nu) + 1j * pulsatile_duct(Y, Z, T / 4, a, Fm, om, nu))
+    n, errs = 0, []
+    for q in range(4):
+        t_q = int(round(3 * T + q * T / 4))
+        while n < t_q:
+            o.set_force((Fm * np.cos(om * n), 0.0, 0.0))
+            f = o.step(f)
+            n += 1
+        o.set_force((Fm * np.cos(om * n), 0.0, 0.0))
+        _, u = o.moments(f)
+        ua = pulsatile_duct(Y, Z, float(n), a, Fm, om, nu)
+        errs.append(np.linalg.norm(u[0][:, :, 0] - ua) / np.linalg.norm(amp))
+        assert np.abs(u[1:]).max() < 1e-6 * np.abs(amp).max()     # no secondary flow
+    return np.array(errs)
+
+
+def test_pulsatile_duct_matches_series(oracle_mod):
+    """Pulsatile duct of Sec. 5.2 (F_x = Fm cos(omega t), square duct of side 2a, walls on
+    y and z, Wo = 3.09, r = 0.5, s = 1 as the paper's first grid) on coarse grids: the
+    x-velocity follows the Fourier-series solution at each quarter of the fourth period,
+    and the error falls at second order when the duct is resolved twice as finely.
+    The force of step n is F(n) and the velocity at t = n is read with F(n)."""
+    e5 = _pulsatile_errors(oracle_mod, 5.0, 0.5, 1.0, 0.05, 3.09)
+    e10 = _pulsatile_errors(oracle_mod, 10.0, 0.5, 1.0, 0.05, 3.09)
+    assert e5.max() < 0.04 and e10.max() < 0.011
+    assert e10.max() < 0.35 * e5.max()
