@@ -33,7 +33,12 @@
  *     takes grad rho from second-order central differences of the current
  *     density field (one-sided second-order differences next to a wall);
  *   - every relaxation rate other than omega_nu, omega_xi is 1 (App. D);
- *   - the initial state is f = f^eq(rho, u) = Q^-1 m^eq (Eq. 10).
+ *   - the initial state is f = f^eq(rho, u) = Q^-1 m^eq (Eq. 10);
+ *   - the optional storage emulation rounds what a reduced-precision store
+ *     keeps: the deviation g_a = f_a - w_a from the rest weights w_a =
+ *     f^eq_a(1, 0), after the collision (and after initialisation), to
+ *     binary16 scaled per direction by 2^(10 - ilogb w_a), or to bfloat16,
+ *     rounding to nearest with ties to even.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -69,6 +74,8 @@ typedef struct {
     double force[3];           /* uniform body force */
     const double *force_field; /* optional per-node force [3][nz][ny][nx], added to force */
     double lid_u;              /* velocity (along x) of the wall at y = ny-1/2; 0 = at rest */
+    int storage_emulation;     /* 0 none; 1 or 2: round every stored deviation g = f - w to
+                                  binary16 (times 2^(10 - ilogb w_a)) or to bfloat16 */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -561,6 +568,53 @@ int or_stream(const or_params *p, const double *ft, double *fout)
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Reduced-precision storage emulation                                       */
+
+/* Round x to the nearest value of a binary floating-point format with p
+ * significand bits and minimum normal exponent emin, ties to even (IEEE 754
+ * roundTiesToEven).  Around |x| in [2^e, 2^(e+1)) the format's values are
+ * spaced 2^(e-p+1); below 2^emin (subnormals) the spacing stays 2^(emin-p+1).
+ * Dividing by a power of two is exact, and rint() rounds ties to even in the
+ * default rounding mode.  Results above the largest finite value become inf. */
+static double round_format(double x, int p, int emin, double maxfinite)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e = ilogb(x);
+    if (e < emin) e = emin;
+    const double q = ldexp(1.0, e - (p - 1));
+    const double r = rint(x / q) * q;
+    return fabs(r) > maxfinite ? copysign(INFINITY, x) : r;
+}
+
+/* binary16: 11 significand bits, emin = -14, largest finite 65504. */
+double or_round_binary16(double x) { return round_format(x, 11, -14, 65504.0); }
+
+/* bfloat16: 8 significand bits, emin = -126, largest finite (2 - 2^-7) 2^127. */
+double or_round_bfloat16(double x) { return round_format(x, 8, -126, ldexp(255.0, 120)); }
+
+/* f_a := w_a + round(f_a - w_a) at every node, per p->storage_emulation. */
+int or_quantize(const or_params *p, double *f)
+{
+    if (!p->storage_emulation) return 0;
+    if (p->storage_emulation != 1 && p->storage_emulation != 2) return -1;
+    const size_t N = nodes(p);
+    const double zero[3] = {0.0, 0.0, 0.0};
+    double w[NQ];
+    if (equilibrium_node(p, 1.0, zero, w)) return -1;
+    for (int a = 0; a < NQ; ++a) {
+        const double sc = ldexp(1.0, 10 - ilogb(w[a]));
+        double *fa = f + a * N;
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < (long)N; ++x) {
+            const double g = fa[x] - w[a];
+            const double q = p->storage_emulation == 1 ? or_round_binary16(g * sc) / sc : or_round_bfloat16(g);
+            fa[x] = w[a] + q;
+        }
+    }
+    return 0;
+}
+
 /* One full time step: collide then stream.  f and fout must not alias. */
 int or_step(const or_params *p, const double *f, double *fout)
 {
@@ -568,6 +622,7 @@ int or_step(const or_params *p, const double *f, double *fout)
     double *ft = (double *)malloc(NQ * N * sizeof(double));
     if (!ft) return -2;
     int err = or_collide_all(p, f, ft);
+    if (!err) err = or_quantize(p, ft);       /* the store keeps the rounded post-collision state */
     if (!err) err = or_stream(p, ft, fout);
     free(ft);
     return err;
@@ -599,7 +654,7 @@ int or_init(const or_params *p, const double *rho, const double *u, double *f)
         err |= equilibrium_node(p, rho[x], uu, feq) ? 1 : 0;
         for (int a = 0; a < NQ; ++a) f[a * N + x] = feq[a];
     }
-    return err ? -1 : 0;
+    return err ? -1 : or_quantize(p, f);
 }
 
 /* rho(x) and u(x) (including the F/2 shift) of every node (Eq. 12). */

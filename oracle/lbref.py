@@ -43,6 +43,7 @@ class _Params(ctypes.Structure):
         ("force", ctypes.c_double * 3),
         ("force_field", ctypes.c_void_p),
         ("lid_u", ctypes.c_double),
+        ("storage_emulation", ctypes.c_int),
     ]
 
 
@@ -58,11 +59,15 @@ def _load():
             ("or_run", [P, d, ctypes.c_int]), ("or_init", [P, d, d, d]),
             ("or_moments", [P, d, d, d]), ("or_collide_node", [P, d, d, d, d]),
             ("or_equilibrium", [P, ctypes.c_double, d, d]),
-            ("or_num_threads", [ctypes.c_int]),
+            ("or_num_threads", [ctypes.c_int]), ("or_quantize", [P, d]),
         ]:
             fn = getattr(_lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        for name in ("or_round_binary16", "or_round_bfloat16"):
+            fn = getattr(_lib, name)
+            fn.argtypes = [ctypes.c_double]
+            fn.restype = ctypes.c_double
         _lib.or_relax_central.argtypes = [P, d, ctypes.c_double, d, d, d, d]
         _lib.or_relax_central.restype = None
         _lib.or_strain_rates.argtypes = [P, d, ctypes.c_double, d, d, ctypes.c_int, d]
@@ -100,11 +105,14 @@ class Oracle:
     ``corr``: CORR_NONE / CORR_LOWMACH / CORR_LOCAL / CORR_FULL.  ``form``: 0
     factored (P, S, F(u) of Sec. 3.1), 1 definitional (Eq. 3a with an LU solve).
     ``walls``: string with any of "x", "y", "z" naming the non-periodic axes.
+    ``storage_emulation``: None, "f16s" or "bf16s": round the stored deviations from the
+    rest weights after every collision and after ``init`` (binary16 scaled by
+    2^(10 - ilogb w_a), or bfloat16; round to nearest, ties to even).
     """
 
     def __init__(self, nx=1, ny=1, nz=1, r=1.0, s=1.0, cs2=None, omega_nu=1.0, omega_xi=1.0,
                  corr=CORR_LOCAL, form=0, walls="", force=(0.0, 0.0, 0.0), force_field=None,
-                 lid_u=0.0, threads=0):
+                 lid_u=0.0, threads=0, storage_emulation=None):
         self.lib = _load()
         if cs2 is None:
             cs2 = min(1.0, r * r, s * s) / 3.0
@@ -120,6 +128,7 @@ class Oracle:
         p.force = (ctypes.c_double * 3)(*force)
         p.force_field = None if self._ff is None else _ptr(self._ff)
         p.lid_u = lid_u
+        p.storage_emulation = {None: 0, "f16s": 1, "bf16s": 2}[storage_emulation]
         self.p = p
         self.pp = ctypes.byref(p)
         if threads:
@@ -194,6 +203,13 @@ class Oracle:
             raise FloatingPointError("oracle run failed")
         return f
 
+    def quantize(self, f) -> np.ndarray:
+        """The rounding of the storage emulation applied to populations f (a copy)."""
+        f = _f64(f).copy()
+        if self.lib.or_quantize(self.pp, _ptr(f)):
+            raise ValueError("bad storage emulation mode")
+        return f
+
     def moments(self, f):
         f = _f64(f)
         rho = np.empty(self.shape)
@@ -220,6 +236,14 @@ class Oracle:
 
     def central_equilibrium(self, rho) -> np.ndarray:
         out = np.empty(27); self.lib.or_central_equilibrium(self.p.cs2, float(rho), _ptr(out)); return out
+
+    @staticmethod
+    def round_binary16(x: float) -> float:
+        return _load().or_round_binary16(float(x))
+
+    @staticmethod
+    def round_bfloat16(x: float) -> float:
+        return _load().or_round_bfloat16(float(x))
 
     @staticmethod
     def velocities() -> np.ndarray:
