@@ -74,6 +74,7 @@ typedef struct {
     double force[3];           /* uniform body force */
     const double *force_field; /* optional per-node force [3][nz][ny][nx], added to force */
     double lid_u;              /* velocity (along x) of the wall at y = ny-1/2; 0 = at rest */
+    int model;                 /* 0 central moments (3DCCM), 1 raw moments (3DCRM, Sec. 7) */
     int storage_emulation;     /* 0 none; 1 or 2: round every stored deviation g = f - w to
                                   binary16 (times 2^(10 - ilogb w_a)) or to bfloat16 */
 } or_params;
@@ -231,28 +232,27 @@ static void central_M(double r, double s, const double u[3], double M[NQ][NQ])
 /* Collision in central moments (App. D)                                     */
 
 #define K(m, n, p) k[g_KI[m][n][p]]
+#define KS(m, n, p) sig[g_KI[m][n][p]]
 #define KT(m, n, p) kt[g_KI[m][n][p]]
 
 /* Diagonal strain rates recovered locally from the non-equilibrium second
  * order central moments (Eq. 44-49, written with the shear/bulk subscripts of
- * App. D).  gr = density gradient (zero unless mode FULL).  al = 1 keeps the
- * 3u^2 aliasing terms, 0 drops them (low-Mach form). */
-static void strain_rates(const or_params *p, const double k[NQ], double rho, const double u[3],
-                         const double gr[3], double al, double d[3])
+ * App. D).  The inputs are the non-equilibrium combinations n2s = k_2s - 3 cs2 rho,
+ * k2d1 = k_200 - k_020, k2d2 = k_200 - k_002.  gr = density gradient (zero unless
+ * mode FULL).  al = 1 keeps the 3u^2 aliasing terms, 0 drops them (low-Mach form). */
+static void strain_rates_n(const or_params *p, double n2s, double k2d1, double k2d2, double rho,
+                           const double u[3], const double gr[3], double al, double d[3])
 {
     const double cs2 = p->cs2, r2 = p->r * p->r, s2 = p->s * p->s;
     const double wn = p->omega_nu, wb = p->omega_xi;
     const double ux = u[0], uy = u[1], uz = u[2];
-    double k2s = K(2,0,0) + K(0,2,0) + K(0,0,2);
-    double k2d1 = K(2,0,0) - K(0,2,0);
-    double k2d2 = K(2,0,0) - K(0,0,2);
     double A = 0.5 * (3.0 * cs2 - 1.0) * ux;
     double B = 0.5 * (3.0 * cs2 - r2) * uy;
     double C = 0.5 * (3.0 * cs2 - s2) * uz;
     double e_sr1 = -A * gr[0] + B * gr[1];
     double e_sr2 = -A * gr[0] + C * gr[2];
     double e_br = -A * gr[0] - B * gr[1] - C * gr[2];
-    double R_b = k2s - 3.0 * cs2 * rho + e_br;
+    double R_b = n2s + e_br;
     double R_s1 = k2d1 + e_sr1;
     double R_s2 = k2d2 + e_sr2;
     double C_sx = (-2.0 * cs2 / wn + 0.5 * (3.0 * cs2 - 1.0) + al * 1.5 * ux * ux) * rho;
@@ -268,16 +268,59 @@ static void strain_rates(const or_params *p, const double k[NQ], double rho, con
     d[2] = (R_s2 - C_sx * d[0]) / C_sz;
 }
 
+static void strain_rates(const or_params *p, const double k[NQ], double rho, const double u[3],
+                         const double gr[3], double al, double d[3])
+{
+    double k2s = K(2,0,0) + K(0,2,0) + K(0,0,2);
+    strain_rates_n(p, k2s - 3.0 * p->cs2 * rho, K(2,0,0) - K(0,2,0), K(2,0,0) - K(0,0,2), rho, u, gr, al, d);
+}
+
+/* Effective equilibria of the combined second-order moments (Eq. 63 of App. D;
+ * corrections of Eq. 30 with the coefficients of Eq. 38-40): eq = base + the
+ * theta terms times the local strain rates + the lambda terms times grad rho.
+ * base = the uncorrected equilibria of (k_2s, k_2d1, k_2d2); n2s, k2d1, k2d2 =
+ * the non-equilibrium parts handed to the strain-rate recovery. */
+static void corrected_equilibria(const or_params *p, double n2s, double k2d1, double k2d2, double rho,
+                                 const double u[3], const double grad_rho[3], const double base[3],
+                                 double eq[3])
+{
+    const double cs2 = p->cs2, r2 = p->r * p->r, s2 = p->s * p->s;
+    const double wn = p->omega_nu, wb = p->omega_xi;
+    const double ux = u[0], uy = u[1], uz = u[2];
+    eq[0] = base[0]; eq[1] = base[1]; eq[2] = base[2];
+    if (p->corr == CORR_NONE) return;
+    double gr[3] = {0.0, 0.0, 0.0};
+    double al = (p->corr == CORR_LOWMACH) ? 0.0 : 1.0;
+    if (p->corr == CORR_FULL) { gr[0] = grad_rho[0]; gr[1] = grad_rho[1]; gr[2] = grad_rho[2]; }
+    double d[3];
+    strain_rates_n(p, n2s, k2d1, k2d2, rho, u, gr, al, d);
+    double tn = 1.0 / wn - 0.5, tb = 1.0 / wb - 0.5;
+    double th_sx = -rho * (al * 3.0 * ux * ux + 3.0 * cs2 - 1.0) * tn;
+    double th_sy = -rho * (al * 3.0 * uy * uy + 3.0 * cs2 - r2) * tn;
+    double th_sz = -rho * (al * 3.0 * uz * uz + 3.0 * cs2 - s2) * tn;
+    double th_bx = -rho * (al * 3.0 * ux * ux + 3.0 * cs2 - 1.0) * tb;
+    double th_by = -rho * (al * 3.0 * uy * uy + 3.0 * cs2 - r2) * tb;
+    double th_bz = -rho * (al * 3.0 * uz * uz + 3.0 * cs2 - s2) * tb;
+    double la_sx = -(3.0 * cs2 - 1.0) * tn * ux;
+    double la_sy = +(3.0 * cs2 - r2) * tn * uy;
+    double la_sz = +(3.0 * cs2 - s2) * tn * uz;
+    double la_bx = -(3.0 * cs2 - 1.0) * tb * ux;
+    double la_by = -(3.0 * cs2 - r2) * tb * uy;
+    double la_bz = -(3.0 * cs2 - s2) * tb * uz;
+    eq[0] = base[0] + th_bx * d[0] + th_by * d[1] + th_bz * d[2]
+          + la_bx * gr[0] + la_by * gr[1] + la_bz * gr[2];
+    eq[1] = base[1] + th_sx * d[0] - th_sy * d[1] + la_sx * gr[0] + la_sy * gr[1];
+    eq[2] = base[2] + th_sx * d[0] - th_sz * d[2] + la_sx * gr[0] + la_sz * gr[2];
+}
+
 /* Post-collision central moments kt from pre-collision central moments k. */
 static void relax_central(const or_params *p, const double k[NQ], double rho, const double u[3],
                           const double F[3], const double grad_rho[3], double kt[NQ])
 {
     const double cs2 = p->cs2, cs4 = cs2 * cs2, cs6 = cs4 * cs2;
-    const double r2 = p->r * p->r, s2 = p->s * p->s;
     const double wn = p->omega_nu, wb = p->omega_xi;
     /* every other relaxation rate is unity (App. D) */
     const double w1 = 1.0, w3 = 1.0, w111 = 1.0, w211 = 1.0, w4 = 1.0, w122 = 1.0, w222 = 1.0;
-    const double ux = u[0], uy = u[1], uz = u[2];
 
     /* B: combine selected moments (App. D, Eq. combinedprecollisioncentramoments) */
     double k2s = K(2,0,0) + K(0,2,0) + K(0,0,2);
@@ -290,33 +333,11 @@ static void relax_central(const or_params *p, const double k[NQ], double rho, co
     double k4d1 = K(2,2,0) + K(2,0,2) - K(0,2,2);
     double k4d2 = K(2,2,0) - K(2,0,2);
 
-    /* effective equilibria of the combined second-order moments (Eq. 63 of
-     * App. D; corrections of Eq. 30 with the coefficients of Eq. 38-40) */
-    double k2s_eq = 3.0 * cs2 * rho, k2d1_eq = 0.0, k2d2_eq = 0.0;
-    if (p->corr != CORR_NONE) {
-        double gr[3] = {0.0, 0.0, 0.0};
-        double al = (p->corr == CORR_LOWMACH) ? 0.0 : 1.0;
-        if (p->corr == CORR_FULL) { gr[0] = grad_rho[0]; gr[1] = grad_rho[1]; gr[2] = grad_rho[2]; }
-        double d[3];
-        strain_rates(p, k, rho, u, gr, al, d);
-        double tn = 1.0 / wn - 0.5, tb = 1.0 / wb - 0.5;
-        double th_sx = -rho * (al * 3.0 * ux * ux + 3.0 * cs2 - 1.0) * tn;
-        double th_sy = -rho * (al * 3.0 * uy * uy + 3.0 * cs2 - r2) * tn;
-        double th_sz = -rho * (al * 3.0 * uz * uz + 3.0 * cs2 - s2) * tn;
-        double th_bx = -rho * (al * 3.0 * ux * ux + 3.0 * cs2 - 1.0) * tb;
-        double th_by = -rho * (al * 3.0 * uy * uy + 3.0 * cs2 - r2) * tb;
-        double th_bz = -rho * (al * 3.0 * uz * uz + 3.0 * cs2 - s2) * tb;
-        double la_sx = -(3.0 * cs2 - 1.0) * tn * ux;
-        double la_sy = +(3.0 * cs2 - r2) * tn * uy;
-        double la_sz = +(3.0 * cs2 - s2) * tn * uz;
-        double la_bx = -(3.0 * cs2 - 1.0) * tb * ux;
-        double la_by = -(3.0 * cs2 - r2) * tb * uy;
-        double la_bz = -(3.0 * cs2 - s2) * tb * uz;
-        k2s_eq = 3.0 * cs2 * rho + th_bx * d[0] + th_by * d[1] + th_bz * d[2]
-               + la_bx * gr[0] + la_by * gr[1] + la_bz * gr[2];
-        k2d1_eq = th_sx * d[0] - th_sy * d[1] + la_sx * gr[0] + la_sy * gr[1];
-        k2d2_eq = th_sx * d[0] - th_sz * d[2] + la_sx * gr[0] + la_sz * gr[2];
-    }
+    /* effective equilibria of the combined second-order moments (App. D) */
+    const double base[3] = {3.0 * cs2 * rho, 0.0, 0.0};
+    double eq[3];
+    corrected_equilibria(p, k2s - 3.0 * cs2 * rho, k2d1, k2d2, rho, u, grad_rho, base, eq);
+    const double k2s_eq = eq[0], k2d1_eq = eq[1], k2d2_eq = eq[2];
 
     /* relaxation (App. D); source central moments: sigma_100 = F (Eq. 11c) */
     double t100 = K(1,0,0) + w1 * (0.0 - K(1,0,0)) + (1.0 - 0.5 * w1) * F[0];
@@ -360,6 +381,80 @@ static void relax_central(const or_params *p, const double k[NQ], double rho, co
     KT(2,1,1) = t211; KT(1,2,1) = t121; KT(1,1,2) = t112;
     KT(1,2,2) = t122; KT(2,1,2) = t212; KT(2,2,1) = t221;
     KT(2,2,2) = t222;
+}
+
+/* Raw-moment equilibria (Eq. 10): the binomial transform of Eq. 9, which is the
+ * product rho mu_m(u_x) mu_n(u_y) mu_p(u_z) with mu_0 = 1, mu_1 = u, mu_2 = cs2 + u^2. */
+static void raw_equilibrium(double cs2, double rho, const double u[3], double meq[NQ])
+{
+    for (int j = 0; j < NQ; ++j) {
+        double v = rho;
+        const int e[3] = {MM[j], MN[j], MP[j]};
+        for (int i = 0; i < 3; ++i) {
+            if (e[i] == 1) v *= u[i];
+            else if (e[i] == 2) v *= cs2 + u[i] * u[i];
+        }
+        meq[j] = v;
+    }
+}
+
+/* Raw moments of the source term (Eq. 11). */
+static void raw_source(const double F[3], const double u[3], double sig[NQ])
+{
+    for (int j = 0; j < NQ; ++j) sig[j] = 0.0;
+    KS(1,0,0) = F[0]; KS(0,1,0) = F[1]; KS(0,0,1) = F[2];
+    KS(1,1,0) = F[0] * u[1] + F[1] * u[0];
+    KS(1,0,1) = F[0] * u[2] + F[2] * u[0];
+    KS(0,1,1) = F[1] * u[2] + F[2] * u[1];
+    KS(2,0,0) = 2.0 * F[0] * u[0];
+    KS(0,2,0) = 2.0 * F[1] * u[1];
+    KS(0,0,2) = 2.0 * F[2] * u[2];
+}
+
+/* Post-collision raw moments mt of the raw-moment scheme (3DCRM: the cuboid
+ * raw-moment formulation of Sec. 3.2, Eq. LBErawmomentcuboidlattice, with the
+ * corrected equilibria of the central scheme, Sec. 7):
+ *   mt = m + B^-1 { Lambda (B m^eq - B m) + (I - Lambda/2) B Phi },
+ * m^eq from Eq. 10, Phi from Eq. 11, Lambda = omega_nu on the off-diagonal and
+ * deviatoric second-order moments, omega_xi on their trace, 1 elsewhere.  For
+ * the groups that B combines above second order all rates are 1, so B and B^-1
+ * cancel there.  The strain rates of the corrections take the second-order
+ * non-equilibrium moments m - m^eq + Phi/2, the quantity that equals the central
+ * non-equilibrium moments (Sec. 2.3 equates the two; with a body force they
+ * differ by Phi/2). */
+static void relax_raw(const or_params *p, const double m[NQ], double rho, const double u[3],
+                      const double F[3], const double grad_rho[3], double mt[NQ])
+{
+    const double wn = p->omega_nu, wb = p->omega_xi;
+    double meq[NQ], sig[NQ];
+    raw_equilibrium(p->cs2, rho, u, meq);
+    raw_source(F, u, sig);
+    /* rate 1 everywhere first: mt = m + (m^eq - m) + Phi/2 */
+    for (int j = 0; j < NQ; ++j) mt[j] = m[j] + 1.0 * (meq[j] - m[j]) + (1.0 - 0.5) * sig[j];
+    mt[g_KI[0][0][0]] = m[g_KI[0][0][0]];
+    /* off-diagonal second-order moments at omega_nu */
+    const int off[3][3] = {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    for (int i = 0; i < 3; ++i) {
+        const int j = g_KI[off[i][0]][off[i][1]][off[i][2]];
+        mt[j] = m[j] + wn * (meq[j] - m[j]) + (1.0 - 0.5 * wn) * sig[j];
+    }
+    /* B: trace and the two deviatoric combinations of the diagonal moments */
+    const int jx = g_KI[2][0][0], jy = g_KI[0][2][0], jz = g_KI[0][0][2];
+    double c2s = m[jx] + m[jy] + m[jz], c2d1 = m[jx] - m[jy], c2d2 = m[jx] - m[jz];
+    const double base[3] = {meq[jx] + meq[jy] + meq[jz], meq[jx] - meq[jy], meq[jx] - meq[jz]};
+    const double s2s = sig[jx] + sig[jy] + sig[jz], s2d1 = sig[jx] - sig[jy], s2d2 = sig[jx] - sig[jz];
+    const double nx = m[jx] - meq[jx] + 0.5 * sig[jx];
+    const double ny = m[jy] - meq[jy] + 0.5 * sig[jy];
+    const double nz = m[jz] - meq[jz] + 0.5 * sig[jz];
+    double eq[3];
+    corrected_equilibria(p, nx + ny + nz, nx - ny, nx - nz, rho, u, grad_rho, base, eq);
+    const double t2s = c2s + wb * (eq[0] - c2s) + (1.0 - 0.5 * wb) * s2s;
+    const double t2d1 = c2d1 + wn * (eq[1] - c2d1) + (1.0 - 0.5 * wn) * s2d1;
+    const double t2d2 = c2d2 + wn * (eq[2] - c2d2) + (1.0 - 0.5 * wn) * s2d2;
+    /* B^-1 */
+    mt[jx] = (t2s + t2d1 + t2d2) / 3.0;
+    mt[jy] = (t2s - 2.0 * t2d1 + t2d2) / 3.0;
+    mt[jz] = (t2s + t2d1 - 2.0 * t2d2) / 3.0;
 }
 
 /* Central-moment equilibria matched to the Maxwellian (Eq. 9). */
@@ -418,6 +513,25 @@ static int collide_node(const or_params *p, const double f[NQ], const double F[3
 {
     double rho, u[3], k[NQ], kt[NQ];
     node_moments(p, f, F, &rho, u);
+    if (p->model == 1) {
+        /* raw moments with the cuboid velocities, relaxed in place of central ones */
+        double m[NQ], mt[NQ], S[NQ];
+        const double zero[3] = {0.0, 0.0, 0.0};
+        if (p->form == 1) {
+            double M[NQ][NQ];
+            central_M(p->r, p->s, zero, M);     /* Eq. 3b: moments about zero velocity */
+            matvec27(M, f, m);
+            relax_raw(p, m, rho, u, F, grad_rho, mt);
+            return lu_solve27(M, mt, ft);
+        }
+        matvec27(g_P, f, m);                    /* m = S P f */
+        scaling_S(p->r, p->s, S);
+        for (int j = 0; j < NQ; ++j) m[j] *= S[j];
+        relax_raw(p, m, rho, u, F, grad_rho, mt);
+        for (int j = 0; j < NQ; ++j) mt[j] /= S[j];   /* f~ = P^-1 S^-1 m~ */
+        matvec27(g_Pinv, mt, ft);
+        return 0;
+    }
     if (p->form == 1) {
         double M[NQ][NQ];
         central_M(p->r, p->s, u, M);     /* Eq. 3a */
@@ -722,3 +836,4 @@ void or_moment_exponents(int *m, int *n, int *p)
     memcpy(m, MM, sizeof(MM)); memcpy(n, MN, sizeof(MN)); memcpy(p, MP, sizeof(MP));
 }
 void or_central_equilibrium(double cs2, double rho, double *keq) { central_equilibrium(cs2, rho, keq); }
+void or_raw_equilibrium(double cs2, double rho, const double *u, double *meq) { setup(); raw_equilibrium(cs2, rho, u, meq); }

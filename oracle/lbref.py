@@ -43,6 +43,7 @@ class _Params(ctypes.Structure):
         ("force", ctypes.c_double * 3),
         ("force_field", ctypes.c_void_p),
         ("lid_u", ctypes.c_double),
+        ("model", ctypes.c_int),
         ("storage_emulation", ctypes.c_int),
     ]
 
@@ -77,7 +78,8 @@ def _load():
                            ("or_matrix_F", [d, d]),
                            ("or_matrix_M", [ctypes.c_double, ctypes.c_double, d, d]),
                            ("or_velocities", [d, d, d]), ("or_moment_exponents", [d, d, d]),
-                           ("or_central_equilibrium", [ctypes.c_double, ctypes.c_double, d])]:
+                           ("or_central_equilibrium", [ctypes.c_double, ctypes.c_double, d]),
+                           ("or_raw_equilibrium", [ctypes.c_double, ctypes.c_double, d, d])]:
             fn = getattr(_lib, name)
             fn.argtypes = args
             fn.restype = None
@@ -105,6 +107,8 @@ class Oracle:
     ``corr``: CORR_NONE / CORR_LOWMACH / CORR_LOCAL / CORR_FULL.  ``form``: 0
     factored (P, S, F(u) of Sec. 3.1), 1 definitional (Eq. 3a with an LU solve).
     ``walls``: string with any of "x", "y", "z" naming the non-periodic axes.
+    ``model``: "central" (3DCCM, the collision in central moments) or "raw" (3DCRM: the
+    same corrected equilibria relaxed in raw moments, Sec. 7).
     ``storage_emulation``: None, "f16s" or "bf16s": round the stored deviations from the
     rest weights after every collision and after ``init`` (binary16 scaled by
     2^(10 - ilogb w_a), or bfloat16; round to nearest, ties to even).
@@ -112,7 +116,7 @@ class Oracle:
 
     def __init__(self, nx=1, ny=1, nz=1, r=1.0, s=1.0, cs2=None, omega_nu=1.0, omega_xi=1.0,
                  corr=CORR_LOCAL, form=0, walls="", force=(0.0, 0.0, 0.0), force_field=None,
-                 lid_u=0.0, threads=0, storage_emulation=None):
+                 lid_u=0.0, threads=0, storage_emulation=None, model="central"):
         self.lib = _load()
         if cs2 is None:
             cs2 = min(1.0, r * r, s * s) / 3.0
@@ -129,6 +133,7 @@ class Oracle:
         p.force_field = None if self._ff is None else _ptr(self._ff)
         p.lid_u = lid_u
         p.storage_emulation = {None: 0, "f16s": 1, "bf16s": 2}[storage_emulation]
+        p.model = {"central": 0, "raw": 1}[model]
         self.p = p
         self.pp = ctypes.byref(p)
         if threads:
@@ -236,6 +241,10 @@ class Oracle:
 
     def central_equilibrium(self, rho) -> np.ndarray:
         out = np.empty(27); self.lib.or_central_equilibrium(self.p.cs2, float(rho), _ptr(out)); return out
+
+    def raw_equilibrium(self, rho, u) -> np.ndarray:
+        u = _f64(u); out = np.empty(27)
+        self.lib.or_raw_equilibrium(self.p.cs2, float(rho), _ptr(u), _ptr(out)); return out
 
     @staticmethod
     def round_binary16(x: float) -> float:
