@@ -310,6 +310,49 @@ def oracle_sample(seconds_target=15.0, cores=None):
                       f"(FP64 C oracle, factored form, OpenMP), {dt:.1f} s"}
 
 
+def run_study(args):
+    """Parameter studies of Secs. 6 and 7 through the library (FP32 storage)."""
+    from paper_2107_14774_gb300 import studies
+    omegas = [float(v) for v in args.omegas.split(",")]
+    emit = lambda d: print(json.dumps(d), flush=True)
+    t0 = time.time()
+    if args.study == "stability":          # Fig. 8: U_max vs omega_nu, both schemes, cs2 = 0.08
+        for (nx, ny, nz, r, s) in [(30, 40, 30, 0.75, 1.0), (30, 60, 30, 0.5, 1.0)]:
+            for model in ("central", "raw"):
+                for wn in omegas:
+                    U = studies.max_stable_lid_velocity(nx, ny, nz, r, s, 0.08, wn, 1.0, model, args.study_steps)
+                    emit({"study": "stability", "grid": [nx, ny, nz], "r": r, "s": s, "model": model,
+                          "omega_nu": wn, "omega_xi": 1.0, "U_max": U, "steps": args.study_steps})
+    elif args.study == "xi":               # Fig. 9: U_max vs omega_nu for omega_xi = 0.5, 1.0, 1.4
+        for wb in (0.5, 1.0, 1.4):
+            for wn in omegas:
+                U = studies.max_stable_lid_velocity(30, 60, 30, 0.5, 1.0, 0.08, wn, wb, "central", args.study_steps)
+                emit({"study": "xi", "grid": [30, 60, 30], "r": 0.5, "s": 1.0, "model": "central",
+                      "omega_nu": wn, "omega_xi": wb, "U_max": U, "steps": args.study_steps})
+    elif args.study == "reynolds":         # Fig. 10: Re_max at U = 0.2, r = 0.5, s = 1, cs2 = 0.08
+        for (nx, ny, nz) in [(40, 80, 40), (50, 100, 50), (90, 180, 90)]:
+            for model in ("central", "raw"):
+                re = studies.max_stable_reynolds(nx, ny, nz, 0.5, 1.0, 0.08, 0.2, model, args.study_steps)
+                emit({"study": "reynolds", "grid": [nx, ny, nz], "r": 0.5, "s": 1.0, "model": model, "U": 0.2,
+                      "Re_max": re, "steps": args.study_steps})
+    else:                                  # Sec. 6: shallow cavity, cubic vs cuboid, Re = 100, Ma = 0.1
+        cubic = studies.shallow_cavity(256, 64, 128, 1.0, 1.0, 1 / 3, 0.1 * (1 / 3) ** 0.5)
+        emit({"study": "cavity", "lattice": "cubic 256x64x128", "r": 1.0, "s": 1.0, "cs2": 1 / 3,
+              "nodes": cubic["nodes"], "steps": cubic["steps"], "seconds": cubic["seconds"], "stable": cubic["stable"],
+              "u_min": float(cubic["u"].min()), "v_max": float(cubic["v"].max()), "v_min": float(cubic["v"].min())})
+        for (nx, nz, r, s) in [(104, 40, 0.406, 1.3), (96, 64, 0.375, 0.75), (96, 48, 0.375, 1.0)]:
+            c = studies.shallow_cavity(nx, 64, nz, r, s, 0.04, 0.1 * 0.2)
+            du = float(np.max(np.abs(np.interp(c["y"], cubic["y"], cubic["u"]) - c["u"])))
+            dv = float(np.max(np.abs(np.interp(c["x"], cubic["x"], cubic["v"]) - c["v"])))
+            emit({"study": "cavity", "lattice": f"cuboid {nx}x64x{nz}", "r": r, "s": s, "cs2": 0.04,
+                  "nodes": c["nodes"], "steps": c["steps"], "seconds": c["seconds"], "stable": c["stable"],
+                  "node_ratio": cubic["nodes"] / c["nodes"], "time_ratio": cubic["seconds"] / c["seconds"],
+                  "max_abs_du_over_U": du, "max_abs_dv_over_U": dv,
+                  "u_min": float(c["u"].min()), "v_max": float(c["v"].max()), "v_min": float(c["v"].min())})
+    emit({"study": args.study, "wall_seconds": time.time() - t0})
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,7 +372,14 @@ def main():
                     help="kernel selection passed to the library (auto = row-staged where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")
+    ap.add_argument("--study", default=None, choices=["stability", "xi", "reynolds", "cavity"],
+                    help="run a parameter study of the paper instead of the benchmark (one JSON line per point): "
+                         "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6")
+    ap.add_argument("--study-steps", type=int, default=100_000, help="steps a stable run must survive")
+    ap.add_argument("--omegas", default="1.6,1.7,1.8,1.9,1.95,1.98", help="omega_nu values of the stability study")
     args = ap.parse_args()
+    if args.study:
+        return run_study(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     WORKLOAD.clear()

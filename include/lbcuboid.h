@@ -104,6 +104,10 @@ typedef struct {
                               thread for 2-byte storage, where the lattice allows it); 1: one
                               node per thread; 2: two nodes per thread without staging;
                               3: row-staged for every storage form (cross-checks, measurements) */
+    int model;             /* collision model: 0 = central moments (3DCCM, Sec. 3.2), 1 = raw
+                              moments with the same corrected equilibria (3DCRM, Sec. 3.2 raw
+                              formulation and Sec. 7); model 1 needs LB_CORR_LOCAL and is not
+                              differentiated by lb_adjoint_ke / lb_collide_vjp */
 } lb_config;
 
 /* Fill *cfg with defaults: FP32 storage, LOCAL corrections, periodic, no

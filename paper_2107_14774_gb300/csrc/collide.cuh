@@ -44,6 +44,13 @@ __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
 
+// The kernels' CORR template word carries the lb_corr mode in its low bits and,
+// in kRawModel, the choice of the raw-moment scheme (3DCRM) instead of the
+// central-moment one.
+constexpr int kRawModel = 16;
+__host__ __device__ constexpr int corr_mode(int c) { return c & 15; }
+__host__ __device__ constexpr bool raw_model(int c) { return (c & kRawModel) != 0; }
+
 template <class V> struct Scalar { using type = V; };
 template <> struct Scalar<F2> { using type = float; };
 
@@ -185,6 +192,7 @@ __device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const
                                                    V Fx, V Fy, V Fz, V grx, V gry, V grz)
 {
     using T = typename Scalar<V>::type;
+    constexpr int CM = corr_mode(CORR);
     const V cs2 = V(P.cs2);
     const V half = V(T(0.5));
     const V dr = m.dr;
@@ -212,13 +220,13 @@ __device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const
 
     // corrected equilibria of the combined moments (App. D, Eq. 63), as deviations
     V E2s = V(T(0)), E2d1 = V(T(0)), E2d2 = V(T(0));
-    if (CORR != LB_CORR_NONE) {
-        const V al = V((CORR == LB_CORR_LOWMACH) ? T(0) : T(1));
+    if (CM != LB_CORR_NONE) {
+        const V al = V((CM == LB_CORR_LOWMACH) ? T(0) : T(1));
         const V ux2 = al * ux * ux, uy2 = al * uy * uy, uz2 = al * uz * uz;
         const V an0 = V(P.an[0]), an1 = V(P.an[1]), an2 = V(P.an[2]);
         // density-gradient terms (FULL only): A, B, C and e-terms
         V ebr = V(T(0)), esr1 = V(T(0)), esr2 = V(T(0));
-        if (CORR == LB_CORR_FULL) {
+        if (CM == LB_CORR_FULL) {
             const V A = half * an0 * ux, B = half * an1 * uy, C = half * an2 * uz;
             esr1 = -A * grx + B * gry;
             esr2 = -A * grx + C * grz;
@@ -251,7 +259,7 @@ __device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const
         E2s = tb * (qx * dxux + qy * dyuy + qz * dzuz);
         E2d1 = tn * (qx * dxux - qy * dyuy);
         E2d2 = tn * (qx * dxux - qz * dzuz);
-        if (CORR == LB_CORR_FULL) {
+        if (CM == LB_CORR_FULL) {
             // lambda coefficients: s-terms -, +, + ; b-terms -, -, -
             const V lx = an0 * ux, ly = an1 * uy, lz = an2 * uz;
             E2s -= tb * (lx * grx + ly * gry + lz * grz);
@@ -282,18 +290,36 @@ __device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const
     o.hFx = half * Fx;
     o.hFy = half * Fy;
     o.hFz = half * Fz;
+    if constexpr (raw_model(CORR)) {
+        // Raw-moment scheme (Sec. 3.2 raw formulation; Sec. 7): relaxing the raw second-
+        // order moments with the raw sources of Eq. 11 leaves them above the central
+        // scheme's post-collision values by half the raw source moments; the
+        // deviations below are taken from the raw equilibria of Eq. 10, and every
+        // raw moment above second order is its equilibrium.
+        o.d200 = fma_(ux, Fx, o.d200);
+        o.d020 = fma_(uy, Fy, o.d020);
+        o.d002 = fma_(uz, Fz, o.d002);
+        o.t110 = fma_(half, fma_(Fx, uy, Fy * ux), o.t110);
+        o.t101 = fma_(half, fma_(Fx, uz, Fz * ux), o.t101);
+        o.t011 = fma_(half, fma_(Fy, uz, Fz * uy), o.t011);
+    }
     return o;
 }
 
 // Back to populations: h~ = f^eq(rho, u) - w + M(u)^-1 (k~ - k^eq) (Apps. E-G).
 // Each post-collision deviation is handed to out(a, value) as soon as it is
-// formed (a store, or a write into a register array).
-template <class V, class T, class Out>
+// formed (a store, or a write into a register array).  RAW: the deviations are
+// raw moments, mapped by P^-1 S^-1 alone (the columns of M(0)^-1).
+template <bool RAW = false, class V, class T, class Out>
 __device__ __forceinline__ void back_transform_to(Out &&out, const PostState<V> &o, const Phys<T> &P)
 {
     const AxisCols<V> X = axis_cols(o.ux, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0]);
     const AxisCols<V> Y = axis_cols(o.uy, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]);
     const AxisCols<V> Z = axis_cols(o.uz, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2]);
+    const V zero = V(T(0));
+    const AxisCols<V> GX = RAW ? axis_cols(zero, P.ic[0], P.ic2[0], P.w0[0], P.wpm[0]) : X;
+    const AxisCols<V> GY = RAW ? axis_cols(zero, P.ic[1], P.ic2[1], P.w0[1], P.wpm[1]) : Y;
+    const AxisCols<V> GZ = RAW ? axis_cols(zero, P.ic[2], P.ic2[2], P.w0[2], P.wpm[2]) : Z;
 
     // rho phi_x phi_y phi_z - w_x w_y w_z = (dr phi_x + dphi_x) P_yz + w_x D_yz with
     // P_yz = phi_y phi_z and D_yz = phi_y phi_z - w_y w_z = dphi_y phi_z + w_y dphi_z
@@ -304,32 +330,32 @@ __device__ __forceinline__ void back_transform_to(Out &&out, const PostState<V> 
 #pragma unroll
     for (int z = 0; z < 3; ++z) {
         // z stage of M^-1 on the sparse non-equilibrium central moments
-        const V A00 = fma_(o.hFz, Z.g1[z], o.d002 * Z.g2[z]);
-        const V A10 = fma_(o.hFx, Z.g0[z], o.t101 * Z.g1[z]);
-        const V A01 = fma_(o.hFy, Z.g0[z], o.t011 * Z.g1[z]);
-        const V A11 = o.t110 * Z.g0[z];
-        const V A20 = o.d200 * Z.g0[z];
-        const V A02 = o.d020 * Z.g0[z];
+        const V A00 = fma_(o.hFz, GZ.g1[z], o.d002 * GZ.g2[z]);
+        const V A10 = fma_(o.hFx, GZ.g0[z], o.t101 * GZ.g1[z]);
+        const V A01 = fma_(o.hFy, GZ.g0[z], o.t011 * GZ.g1[z]);
+        const V A11 = o.t110 * GZ.g0[z];
+        const V A20 = o.d200 * GZ.g0[z];
+        const V A02 = o.d020 * GZ.g0[z];
 #pragma unroll
         for (int y = 0; y < 3; ++y) {
-            const V B0 = fma_(A00, Y.g0[y], fma_(A01, Y.g1[y], A02 * Y.g2[y]));
-            const V B1 = fma_(A10, Y.g0[y], A11 * Y.g1[y]);
-            const V B2 = A20 * Y.g0[y];
+            const V B0 = fma_(A00, GY.g0[y], fma_(A01, GY.g1[y], A02 * GY.g2[y]));
+            const V B1 = fma_(A10, GY.g0[y], A11 * GY.g1[y]);
+            const V B2 = A20 * GY.g0[y];
             const V Pyz = Y.phi[y] * Z.phi[z];
             const V Dyz = fma_(Y.dphi[y], Z.phi[z], Y.w[y] * Z.dphi[z]);
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
                 const V heq = fma_(ax[x], Pyz, X.w[x] * Dyz);
-                out(dir_of(x - 1, y - 1, z - 1), fma_(B0, X.g0[x], fma_(B1, X.g1[x], fma_(B2, X.g2[x], heq))));
+                out(dir_of(x - 1, y - 1, z - 1), fma_(B0, GX.g0[x], fma_(B1, GX.g1[x], fma_(B2, GX.g2[x], heq))));
             }
         }
     }
 }
 
-template <class V, class T>
+template <bool RAW = false, class V, class T>
 __device__ __forceinline__ void back_transform(V (&h)[Q], const PostState<V> &o, const Phys<T> &P)
 {
-    back_transform_to([&](int a, V v) { h[a] = v; }, o, P);
+    back_transform_to<RAW>([&](int a, V v) { h[a] = v; }, o, P);
 }
 
 // One collision, in place on the deviations h of one node (Sec. 3.2 steps, App. D).
@@ -339,7 +365,7 @@ __device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T F
 {
     const RawMoments<T> m = raw_moments(h, P);
     const PostState<T> o = relax_node<T, CORR>(m, P, Fx, Fy, Fz, grx, gry, grz);
-    back_transform(h, o, P);
+    back_transform<raw_model(CORR)>(h, o, P);
     NodeMacro<T> out;
     out.rho = T(1) + o.dr;
     out.ux = o.ux;
@@ -356,7 +382,7 @@ __device__ __forceinline__ void collide_pair(const F2 (&h)[Q], Out &&out, const 
     const RawMoments<F2> m = raw_moments(h, P);
     const F2 z(0.f);
     const PostState<F2> o = relax_node<F2, CORR>(m, P, F0, F1, F2_, z, z, z);
-    back_transform_to(out, o, P);
+    back_transform_to<raw_model(CORR)>(out, o, P);
 }
 
 // Equilibrium deviations h^eq_a = f^eq_a(rho, u) - w_a (init and moving walls).

@@ -13,6 +13,14 @@
 #include "lbcuboid.h"
 #include "ops.cuh"
 
+// The launchers (and with them every kernel) are instantiated once per storage
+// form in step_*.cu, which compile in parallel; this file only calls them.
+extern template struct lbc::Ops<LB_F64>;
+extern template struct lbc::Ops<LB_F32>;
+extern template struct lbc::Ops<LB_F32_SHIFTED>;
+extern template struct lbc::Ops<LB_F16_SHIFTED>;
+extern template struct lbc::Ops<LB_BF16_SHIFTED>;
+
 using namespace lbc;
 
 namespace {
@@ -99,6 +107,7 @@ LaunchArgs launch_args(const lb_ctx *c)
         a.scale[q] = c->scale[q];
     }
     a.corr = c->cfg.corr;
+    a.model = c->cfg.model;
     a.stream = c->stream;
     a.force_field = c->force_field;
     a.rho_field = c->rho_field;
@@ -213,6 +222,9 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (cfg->rounding < 0 || cfg->rounding > 1) return fail(LB_EINVAL, "lb_create_ex: bad rounding mode");
     if (cfg->rounding == 1 && cfg->storage != LB_F16_SHIFTED && cfg->storage != LB_BF16_SHIFTED)
         return fail(LB_EINVAL, "lb_create_ex: stochastic rounding applies to FP16/BF16 storage only");
+    if (cfg->model < 0 || cfg->model > 1) return fail(LB_EINVAL, "lb_create_ex: bad collision model");
+    if (cfg->model == 1 && cfg->corr != LB_CORR_LOCAL)
+        return fail(LB_EINVAL, "lb_create_ex: the raw-moment model runs with LB_CORR_LOCAL only");
     if (cfg->lid_u != 0.0 && !(cfg->wall_mask & LB_WALL_Y))
         return fail(LB_EINVAL, "lb_create_ex: a moving lid needs walls normal to y");
     const double r = cfg->r_y, s = cfg->r_z;
@@ -535,6 +547,7 @@ lb_status lb_adjoint_ke(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2],
     if (!c || !dJdF || !dJdomega) return fail(LB_EINVAL, "lb_adjoint_ke: null argument");
     if (T < 1 || K < 1) return fail(LB_EINVAL, "lb_adjoint_ke: T and K must be >= 1");
     if (c->cfg.corr == LB_CORR_FULL) return fail(LB_EINVAL, "lb_adjoint_ke: corrections FULL are not supported");
+    if (c->cfg.model != 0) return fail(LB_EINVAL, "lb_adjoint_ke: the raw-moment model is not supported");
     if (c->cfg.lid_u != 0.0) return fail(LB_EINVAL, "lb_adjoint_ke: a moving lid is not supported");
     if (c->cfg.rounding != 0) return fail(LB_EINVAL, "lb_adjoint_ke: needs round-to-nearest storage");
     if (K > T) K = T;
@@ -606,6 +619,7 @@ lb_status lb_collide_vjp(lb_ctx *c, long long n, const void *f, const void *F, c
     if (!c || !f || !F || !lam || !f_bar || !F_bar || !w_bar || n < 1)
         return fail(LB_EINVAL, "lb_collide_vjp: bad argument");
     if (c->cfg.corr == LB_CORR_FULL) return fail(LB_EINVAL, "lb_collide_vjp: corrections FULL are not supported");
+    if (c->cfg.model != 0) return fail(LB_EINVAL, "lb_collide_vjp: the raw-moment model is not supported");
     for (const void *p : {f, F, lam, (const void *)f_bar, (const void *)F_bar})
         if (!is_device_pointer(p)) return fail(LB_EINVAL, "lb_collide_vjp: device pointers required");
     Scratch s;

@@ -23,6 +23,7 @@ struct LaunchArgs {
     double w[Q];
     float scale[Q];
     int corr;
+    int model;                // 0 central moments, 1 raw moments (LOCAL corrections only)
     cudaStream_t stream;
     const void *force_field;  // device, compute type, [3][N] or null
     void *rho_field;          // device, compute type, [N] (FULL) or null
@@ -117,8 +118,12 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
                                                                    (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
         break;
     case LB_CORR_LOCAL:
-        k_step<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
-                                                                 ff, rf, (T)a.lid_u, a.sr_key);
+        if (a.model == 1)
+            k_step<ST, LB_CORR_LOCAL | kRawModel><<<grid, block, 0, a.stream>>>(
+                s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
+        else
+            k_step<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1],
+                                                                     (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
         break;
     default:
         k_step<ST, LB_CORR_FULL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
@@ -135,6 +140,7 @@ template <int ST>
 bool Ops<ST>::use_pair(const LaunchArgs &a)
 {
     if (ST == LB_F64 || a.kernel == 1) return false;   // (kernel 3 falls back here where staging does not apply)
+    if (a.model == 1 && a.sr_key != 0) return false;   // raw model with stochastic rounding: one node per thread
     return (a.g.nx % 2 == 0) && !a.g.wall[0] && a.lid_u == 0.0 && a.corr != LB_CORR_FULL &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
@@ -179,7 +185,10 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
                                                                                           ff, 0u);
             break;
         default:
-            if (sr)
+            if (a.model == 1)
+                k_step_pair<ST, LB_CORR_LOCAL | kRawModel, ZC, false><<<grid, block, 0, a.stream>>>(
+                    ptr, a.g, P, D, F0, F1, F2, ff, 0u);
+            else if (sr)
                 k_step_pair<ST, LB_CORR_LOCAL, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
                                                                                        a.sr_key);
             else
@@ -198,7 +207,7 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
 template <int ST>
 bool Ops<ST>::use_bulk(const LaunchArgs &a)
 {
-    if (ST == LB_F64 || a.corr != LB_CORR_LOCAL || !a.err) return false;
+    if (ST == LB_F64 || a.corr != LB_CORR_LOCAL || a.model != 0 || !a.err) return false;
     // automatic choice: 4-byte storage on rows of at most 512 nodes (two CTAs per SM);
     // wider rows leave one CTA of 8 warps per SM, where the two-node kernel measured faster
     if (a.kernel != 3 && (a.kernel != 0 || sizeof(S) != 4 || a.g.nx > 512)) return false;
@@ -391,10 +400,12 @@ const char *Ops<ST>::step_kernel_name(const LaunchArgs &a)
         snprintf(buf, sizeof(buf), "k_step_bulk<%s,%s,%d,%d,%d>", storage_name(ST), corr_name(a.corr), nxmax, ns,
                  minb);
     } else if (use_pair(a)) {
-        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s,%d,%s>", storage_name(ST), corr_name(a.corr), kPairPlanes,
+        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s%s,%d,%s>", storage_name(ST), corr_name(a.corr),
+                 a.model == 1 ? "|RAW" : "", kPairPlanes,
                  (a.sr_key != 0 && sizeof(S) == 2) ? "true" : "false");
     } else {
-        snprintf(buf, sizeof(buf), "k_step<%s,%s>", storage_name(ST), corr_name(a.corr));
+        snprintf(buf, sizeof(buf), "k_step<%s,%s%s>", storage_name(ST), corr_name(a.corr),
+                 a.model == 1 ? "|RAW" : "");
     }
     return buf;
 }

@@ -39,11 +39,13 @@ class Lattice:
     kernel: "auto" (row-staged or two-node kernel where possible), "one" (one node per thread),
     "pair" (two nodes per thread, no staging) or "staged" (row-staged for every storage form).
     rounding: "nearest" or "stochastic" (FP16/BF16 storage only).
+    model: "central" (3DCCM) or "raw" (3DCRM: raw moments relaxed with the same corrected
+    equilibria; LOCAL corrections only).
     """
 
     def __init__(self, nx, ny, nz, r_y=1.0, r_z=1.0, nu=0.01, zeta=0.0, cs2=0.0, storage="f32",
                  corr="local", walls="", force=(0.0, 0.0, 0.0), lid_u=0.0, stream=None, device=None,
-                 kernel="auto", rounding="nearest", rounding_seed=0):
+                 kernel="auto", rounding="nearest", rounding_seed=0, model="central"):
         self.lib = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
@@ -60,6 +62,7 @@ class Lattice:
         cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3}[kernel]
         cfg.rounding = {"nearest": 0, "stochastic": 1}[rounding]
         cfg.rounding_seed = rounding_seed
+        cfg.model = {"central": 0, "raw": 1}[model]
         self.cfg = cfg
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -150,6 +153,15 @@ class Lattice:
         if st != _lib.LB_OK and not (allow_unstable and st == _lib.LB_EUNSTABLE):
             check(st)
         return np.array(list(out))
+
+    def is_stable(self) -> bool:
+        """lb_reduce's verdict: False once a density is non-positive or not finite."""
+        out = (ctypes.c_double * 4)()
+        st = self.lib.lb_reduce(self.ctx, out)
+        if st == _lib.LB_EUNSTABLE:
+            return False
+        check(st)
+        return bool(np.all(np.isfinite(np.array(list(out)))))
 
     def populations(self, out=None):
         """lb_get_populations: pre-collision f [27,nz,ny,nx]."""

@@ -1,0 +1,45 @@
+"""The study drivers of Secs. 6-7: bisection logic on the CPU, one small run of each
+driver on the GPU."""
+import math
+
+import numpy as np
+import pytest
+
+
+def test_bisect_finds_monotone_threshold():
+    from paper_2107_14774_gb300.studies import bisect
+    calls = []
+
+    def stable(x):
+        calls.append(x)
+        return x <= 0.137
+
+    x = bisect(stable, 0.0, 0.4, 0.005)
+    assert 0.137 - 0.005 <= x <= 0.137 and len(calls) <= 8
+    assert bisect(lambda v: True, 0.0, 0.4, 0.005) == 0.4
+    assert bisect(lambda v: False, 0.0, 0.4, 0.005) < 0.005
+
+
+@pytest.mark.gpu
+def test_stability_driver_small():
+    """A tiny cavity: a lid at rest-like speed survives, the bisected threshold lies inside
+    the bracket, and the raw scheme's threshold is no higher than the central one's at a
+    low viscosity (Sec. 7)."""
+    from paper_2107_14774_gb300 import studies
+    lat = studies.lid_cavity(12, 16, 12, 0.75, 1.0, 0.08, 0.01, 1.5)
+    assert studies.survives(lat, 500, 250)
+    lat.close()
+    u_c = studies.max_stable_lid_velocity(12, 16, 12, 0.75, 1.0, 0.08, 1.97, steps=3000, u_hi=0.5, tol=0.02)
+    u_r = studies.max_stable_lid_velocity(12, 16, 12, 0.75, 1.0, 0.08, 1.97, model="raw", steps=3000, u_hi=0.5,
+                                          tol=0.02)
+    print("U_max central %.3f raw %.3f" % (u_c, u_r))
+    assert 0.0 < u_c <= 0.5 and 0.0 < u_r <= 0.5
+
+
+@pytest.mark.gpu
+def test_shallow_cavity_driver_small():
+    from paper_2107_14774_gb300 import studies
+    c = studies.shallow_cavity(32, 8, 16, 1.0, 1.0, 1 / 3, 0.05, Re=20.0, transits=3.0)
+    assert c["stable"] and c["steps"] == round(3.0 * 32 / 0.05)
+    assert c["u"].shape == (8,) and c["v"].shape == (32,)
+    assert c["u"][-1] > 0.0 > c["u"].min()          # dragged along under the lid, return flow below
