@@ -324,11 +324,13 @@ def run_study(args):
                     emit({"study": "stability", "grid": [nx, ny, nz], "r": r, "s": s, "model": model,
                           "omega_nu": wn, "omega_xi": 1.0, "U_max": U, "steps": args.study_steps})
     elif args.study == "xi":               # Fig. 9: U_max vs omega_nu for omega_xi = 0.5, 1.0, 1.4
-        for wb in (0.5, 1.0, 1.4):
-            for wn in omegas:
-                U = studies.max_stable_lid_velocity(30, 60, 30, 0.5, 1.0, 0.08, wn, wb, "central", args.study_steps)
-                emit({"study": "xi", "grid": [30, 60, 30], "r": 0.5, "s": 1.0, "model": "central",
-                      "omega_nu": wn, "omega_xi": wb, "U_max": U, "steps": args.study_steps})
+        for corr in ("local", "none"):
+            for wb in (0.5, 1.0, 1.4):
+                for wn in omegas:
+                    U = studies.max_stable_lid_velocity(30, 60, 30, 0.5, 1.0, 0.08, wn, wb, "central",
+                                                        args.study_steps, corr=corr)
+                    emit({"study": "xi", "grid": [30, 60, 30], "r": 0.5, "s": 1.0, "model": "central",
+                          "corr": corr, "omega_nu": wn, "omega_xi": wb, "U_max": U, "steps": args.study_steps})
     elif args.study == "reynolds":         # Fig. 10: Re_max at U = 0.2, r = 0.5, s = 1, cs2 = 0.08
         for (nx, ny, nz) in [(40, 80, 40), (50, 100, 50), (90, 180, 90)]:
             for model in ("central", "raw"):
@@ -376,7 +378,8 @@ def main():
                     help="run a parameter study of the paper instead of the benchmark (one JSON line per point): "
                          "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6")
     ap.add_argument("--study-steps", type=int, default=100_000, help="steps a stable run must survive")
-    ap.add_argument("--omegas", default="1.6,1.7,1.8,1.9,1.95,1.98", help="omega_nu values of the stability study")
+    ap.add_argument("--omegas", default="1.5,1.6,1.7,1.8,1.9,1.95,1.98",
+                    help="omega_nu values of the stability studies")
     args = ap.parse_args()
     if args.study:
         return run_study(args)
@@ -436,6 +439,8 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample()
+        one = oracle_sample(seconds_target=1.0, cores=1)     # one step on one core
+        cpu["single_core"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
     line = {"metric": METRIC, "value": round(r["mlups"], 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_var == "f64" else "f32", "data": "synthetic", "config": config,

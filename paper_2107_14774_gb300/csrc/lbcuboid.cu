@@ -83,6 +83,11 @@ struct lb_ctx {
     bool fresh;
     int *err;               // error word of the bounded waits of the staged kernel
     int sm_count;
+    // CUDA graphs of kGraphSteps consecutive steps starting from buffer 0 / 1, with
+    // the launch arguments they were captured with; graph_off after a failed capture
+    cudaGraphExec_t graph[2];
+    LaunchArgs graph_key[2];
+    bool graph_off;
 };
 
 namespace {
@@ -94,6 +99,7 @@ unsigned step_key(const lb_ctx *c);
 LaunchArgs launch_args(const lb_ctx *c)
 {
     LaunchArgs a;
+    std::memset(&a, 0, sizeof(a));   // padding included: graphs are keyed by the bytes of a
     a.g = c->g;
     a.r = c->cfg.r_y;
     a.s = c->cfg.r_z;
@@ -141,6 +147,56 @@ cudaError_t dispatch(int st, F &&f)
     default: return f(Ops<LB_BF16_SHIFTED>());
     }
 }
+
+// Steps per CUDA graph.  On small lattices one step takes less time than a kernel
+// launch, so lb_step replays a captured run of kGraphSteps launches (an even number:
+// the ping-pong buffers end where they started) while the launch arguments stay the
+// same.  Graphs are used on a non-default stream with round-to-nearest storage (the
+// stochastic-rounding key changes every step) once a step has run with the same
+// arguments outside the capture.
+constexpr int kGraphSteps = 64;
+
+void drop_graph(lb_ctx *c, int p)
+{
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+    c->graph[p] = nullptr;
+}
+
+// The graph for the current buffer and arguments, captured on first use; null when
+// capture is not possible (graphs are then off for this context).
+cudaGraphExec_t graph_for(lb_ctx *c, const LaunchArgs &a)
+{
+    const int p = c->cur;
+    if (c->graph[p] && std::memcmp(&c->graph_key[p], &a, sizeof(a)) == 0) return c->graph[p];
+    drop_graph(c, p);
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_off = true;
+        return nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    int cur = p;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+        const void *src = c->buf[cur];
+        void *dst = c->buf[cur ^ 1];
+        e = dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); });
+        cur ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    cudaGraphExec_t x = nullptr;
+    if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&x, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !x) {
+        cudaGetLastError();
+        c->graph_off = true;
+        return nullptr;
+    }
+    c->graph[p] = x;
+    c->graph_key[p] = a;
+    return x;
+}
+
 
 bool is_device_pointer(const void *p)
 {
@@ -300,6 +356,8 @@ void lb_destroy(lb_ctx *c)
     cudaFree(c->out4);
     cudaFree(c->status);
     cudaFree(c->err);
+    drop_graph(c, 0);
+    drop_graph(c, 1);
     delete c;
 }
 
@@ -355,14 +413,26 @@ lb_status lb_step(lb_ctx *c, int n)
 {
     if (!c) return fail(LB_EINVAL, "lb_step: null context");
     if (n < 0) return fail(LB_EINVAL, "lb_step: n must be >= 0");
-    for (int i = 0; i < n; ++i) {
+    bool plain_done = false;   // one step with these arguments ran outside a capture
+    for (int i = 0; i < n;) {
         const LaunchArgs a = launch_args(c);
+        if (plain_done && n - i >= kGraphSteps && !c->graph_off && c->stream != nullptr && c->cfg.rounding == 0) {
+            cudaGraphExec_t x = graph_for(c, a);
+            if (x) {
+                LB_CUDA(cudaGraphLaunch(x, c->stream));
+                i += kGraphSteps;
+                c->t += kGraphSteps;
+                continue;
+            }
+        }
         const void *src = c->buf[c->cur];
         void *dst = c->buf[c->cur ^ 1];
         LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); }));
         c->cur ^= 1;
         ++c->t;
+        plain_done = !c->fresh;
         c->fresh = false;
+        ++i;
     }
     return LB_OK;
 }

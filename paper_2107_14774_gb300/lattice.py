@@ -106,6 +106,19 @@ class Lattice:
     def time_step(self) -> int:
         return self.lib.lb_time_step(self.ctx)
 
+    def _after_caller(self):
+        """Order the context's stream after the caller's current stream (inputs written
+        there, output buffers allocated there)."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _before_caller(self):
+        """Order the caller's current stream after the context's stream (device outputs)."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+
     def _real(self, x, shape):
         if isinstance(x, np.ndarray):
             x = torch.from_numpy(x)
@@ -119,6 +132,7 @@ class Lattice:
         """lb_init: f := f^eq(rho, u) at every node."""
         rho = self._real(rho, self.shape)
         u = self._real(u, (3,) + self.shape)
+        self._after_caller()
         check(self.lib.lb_init(self.ctx, _ptr(rho), _ptr(u)))
         self._keep = (rho, u)  # keep inputs alive until the stream has consumed them
         return self
@@ -129,6 +143,7 @@ class Lattice:
             check(self.lib.lb_set_force_field(self.ctx, None))
             return
         force = self._real(force, (3,) + self.shape)
+        self._after_caller()
         check(self.lib.lb_set_force_field(self.ctx, _ptr(force)))
         self._keep_force = force
 
@@ -143,7 +158,9 @@ class Lattice:
             rho = torch.empty(self.shape, dtype=self.dtype, device=self.device)
         if u is None:
             u = torch.empty((3,) + self.shape, dtype=self.dtype, device=self.device)
+        self._after_caller()
         check(self.lib.lb_moments(self.ctx, _ptr(rho), _ptr(u)))
+        self._before_caller()
         return rho, u
 
     def reduce(self, allow_unstable: bool = False) -> np.ndarray:
@@ -167,11 +184,14 @@ class Lattice:
         """lb_get_populations: pre-collision f [27,nz,ny,nx]."""
         if out is None:
             out = torch.empty((27,) + self.shape, dtype=self.dtype, device=self.device)
+        self._after_caller()
         check(self.lib.lb_get_populations(self.ctx, _ptr(out)))
+        self._before_caller()
         return out
 
     def set_populations(self, f):
         f = self._real(f, (27,) + self.shape)
+        self._after_caller()
         check(self.lib.lb_set_populations(self.ctx, _ptr(f)))
         return self
 
@@ -182,10 +202,13 @@ class Lattice:
         """lb_get_state: raw stored state (bit-exact checkpoint)."""
         if out is None:
             out = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        self._after_caller()
         check(self.lib.lb_get_state(self.ctx, _ptr(out)))
+        self._before_caller()
         return out
 
     def set_state(self, state, time_step: int = 0):
+        self._after_caller()
         check(self.lib.lb_set_state(self.ctx, _ptr(state), int(time_step)))
         return self
 
@@ -213,7 +236,9 @@ class Lattice:
             dJdF = torch.empty((3,) + self.shape, dtype=self.dtype, device=self.device)
         dw = (ctypes.c_double * 2)()
         J = ctypes.c_double()
+        self._after_caller()
         check(self.lib.lb_adjoint_ke(self.ctx, int(T), int(K), _ptr(dJdF), dw, ctypes.byref(J)))
+        self._before_caller()
         return J.value, dJdF, (dw[0], dw[1])
 
     def collide_vjp(self, f, F, lam):
@@ -223,5 +248,7 @@ class Lattice:
         fb = torch.empty_like(f)
         Fb = torch.empty_like(F)
         wb = (ctypes.c_double * 2)()
+        self._after_caller()
         check(self.lib.lb_collide_vjp(self.ctx, n, _ptr(f), _ptr(F), _ptr(lam), _ptr(fb), _ptr(Fb), wb))
+        self._before_caller()
         return fb, Fb, (wb[0], wb[1])

@@ -18,11 +18,11 @@ import torch
 from .lattice import Lattice
 
 
-def lid_cavity(nx, ny, nz, r, s, cs2, U, omega_nu, omega_xi=1.0, model="central", storage="f32"):
+def lid_cavity(nx, ny, nz, r, s, cs2, U, omega_nu, omega_xi=1.0, model="central", storage="f32", corr="local"):
     """Closed box (walls on every axis) with the wall at y = ny - 1/2 moving along x at U,
-    at rest with unit density."""
+    at rest with unit density, on its own stream (lb_step then replays CUDA graphs)."""
     lat = Lattice(nx, ny, nz, r_y=r, r_z=s, nu=0.01, cs2=cs2, storage=storage, walls="xyz", lid_u=U,
-                  model=model)
+                  model=model, corr=corr, stream=torch.cuda.Stream())
     lat.set_rates(omega_nu, omega_xi)
     dt = torch.float64 if storage == "f64" else torch.float32
     lat.init(torch.ones((nz, ny, nx), dtype=dt, device=lat.device),
@@ -58,11 +58,11 @@ def bisect(stable, lo, hi, tol):
 
 
 def max_stable_lid_velocity(nx, ny, nz, r, s, cs2, omega_nu, omega_xi=1.0, model="central", steps=100_000,
-                            u_hi=0.4, tol=0.005, storage="f32"):
+                            u_hi=0.6, tol=0.005, storage="f32", corr="local"):
     """Sec. 7 stability test: the largest lid velocity U (to within tol) for which the
     cavity stays stable for `steps` steps."""
     def stable(U):
-        lat = lid_cavity(nx, ny, nz, r, s, cs2, U, omega_nu, omega_xi, model, storage)
+        lat = lid_cavity(nx, ny, nz, r, s, cs2, U, omega_nu, omega_xi, model, storage, corr)
         try:
             return survives(lat, steps)
         finally:
@@ -94,7 +94,8 @@ def shallow_cavity(nx, ny, nz, r, s, cs2, U, Re=100.0, transits=30.0, storage="f
     coordinates normalised by H and L), the steps and the device time in seconds."""
     L = float(nx)
     nu = U * L / Re
-    lat = Lattice(nx, ny, nz, r_y=r, r_z=s, nu=nu, cs2=cs2, storage=storage, walls="xyz", lid_u=U)
+    lat = Lattice(nx, ny, nz, r_y=r, r_z=s, nu=nu, cs2=cs2, storage=storage, walls="xyz", lid_u=U,
+                  stream=torch.cuda.Stream())
     dt = torch.float64 if storage == "f64" else torch.float32
     lat.init(torch.ones((nz, ny, nx), dtype=dt, device=lat.device),
              torch.zeros((3, nz, ny, nx), dtype=dt, device=lat.device))

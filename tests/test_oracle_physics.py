@@ -245,3 +245,44 @@ def test_pulsatile_duct_matches_series(oracle_mod):
     e10 = _pulsatile_errors(oracle_mod, 10.0, 0.5, 1.0, 0.05, 3.09)
     assert e5.max() < 0.04 and e10.max() < 0.011
     assert e10.max() < 0.35 * e5.max()
+
+
+def _sound_decay_ratio(oracle_mod, axis, omega_xi, corr):
+    """Fitted decay rate of a standing sound wave along one axis over the rate of Eq. 51/53."""
+    from scipy.optimize import curve_fit
+    r, s, cs2, wn = 0.5, 1.3, 1 / 12, 1.2
+    nu = cs2 * (1 / wn - 0.5)
+    xi = 2 * cs2 / 3 * (1 / omega_xi - 0.5)
+    n = [1, 1, 1]
+    n[axis] = 64
+    c = (1.0, r, s)[axis]
+    k = 2 * np.pi / (64 * c)
+    o = oracle_mod.Oracle(*n, r=r, s=s, cs2=cs2, omega_nu=wn, omega_xi=omega_xi,
+                          corr=getattr(oracle_mod, "CORR_" + corr))
+    x = (np.arange(64) + 0.5) * c
+    shape = (n[2], n[1], n[0])
+    f = o.init((1 + 1e-4 * np.cos(k * x)).reshape(shape), np.zeros((3,) + shape))
+    period = 2 * np.pi / (np.sqrt(cs2) * k)
+    ts, amp = [], []
+    for t in range(int(3 * period)):
+        r_t, _ = o.moments(f)
+        ts.append(t)
+        amp.append(float(np.sum((r_t.ravel() - 1) * np.cos(k * x)) / np.sum(np.cos(k * x) ** 2)))
+        f = o.step(f)
+    model = lambda t, A, G, w, ph: A * np.exp(-G * t) * np.cos(w * t + ph)
+    p, _ = curve_fit(model, np.array(ts, float), np.array(amp), p0=(1e-4, 1e-4, np.sqrt(cs2) * k, 0.0))
+    return p[1] / (0.5 * k * k * (4 * nu / 3 + xi))
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("omega_xi", [0.5, 1.0, 1.4])
+def test_sound_wave_attenuation_gives_eq53_bulk_viscosity(oracle_mod, axis, omega_xi):
+    """A standing sound wave rho = 1 + A cos(k x_axis) decays at Gamma = k^2 (4 nu / 3 + xi) / 2
+    (the longitudinal momentum diffusivity of Eq. 51) with xi, nu from Eq. 53 along every
+    axis of a cuboid lattice (spacings 1, r = 0.5, s = 1.3): this pins the bulk rate
+    omega_xi.  Without the corrections the normal stress is off along the axes where
+    3 cs2 != c^2 (x and z here; Eq. 22)."""
+    assert _sound_decay_ratio(oracle_mod, axis, omega_xi, "LOCAL") == pytest.approx(1.0, abs=0.01)
+    if omega_xi == 1.0:
+        bias = _sound_decay_ratio(oracle_mod, axis, omega_xi, "NONE")
+        assert (bias > 2.0) if axis != 1 else (bias == pytest.approx(1.0, abs=0.01))
