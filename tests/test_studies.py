@@ -43,3 +43,20 @@ def test_shallow_cavity_driver_small():
     assert c["stable"] and c["steps"] == round(3.0 * 32 / 0.05)
     assert c["u"].shape == (8,) and c["v"].shape == (32,)
     assert c["u"][-1] > 0.0 > c["u"].min()          # dragged along under the lid, return flow below
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("model", ["central", "raw"])
+def test_study_cavity_matches_oracle(oracle_mod, model):
+    """The configuration the Sec. 7 studies run (closed box, lid, rates set directly with
+    omega_xi = 0.5, own stream, graph replay), FP64 storage, 150 steps: within 1e-12 of
+    the oracle."""
+    from paper_2107_14774_gb300 import studies
+    n, r, s, cs2, U = (12, 16, 12), 0.75, 1.0, 0.08, 0.05
+    lat = studies.lid_cavity(*n, r, s, cs2, U, 1.9, 0.5, model=model, storage="f64")
+    lat.step(150)
+    fg = lat.populations().cpu().numpy()
+    lat.close()
+    o = oracle_mod.Oracle(*n, r=r, s=s, cs2=cs2, omega_nu=1.9, omega_xi=0.5, walls="xyz", lid_u=U, model=model)
+    f = o.run(o.init(np.ones(n[::-1]), np.zeros((3,) + n[::-1])), 150)
+    assert np.linalg.norm(fg - f) / np.linalg.norm(f) < 1e-12
