@@ -380,12 +380,18 @@ __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], c
 // ZC consecutive planes per thread: the loads of plane k+1 are issued before the
 // collision of plane k, so that every warp keeps memory requests in flight while
 // it computes (software pipelining across z).
+// Resident CTAs per SM requested from the compiler.  Five CTAs of 128 threads (at most
+// 102 registers; the compiler takes 96 and spills a few words) hide the load latency
+// better than four at 126 registers: measured on GB300, BF16 storage 35.7 -> 39.8 GLUPS,
+// FP32 on 768-wide rows 25.2 -> 31.4 GLUPS; six CTAs (80 registers) spill too much.
 #ifndef LBC_PAIR_MINBLOCKS
-#define LBC_PAIR_MINBLOCKS 1
+#define LBC_PAIR_MINBLOCKS 5
 #endif
-// (the stochastic-rounding variant keeps 4 CTAs per SM, i.e. <= 128 registers)
+#ifndef LBC_PAIR_SR_MINBLOCKS
+#define LBC_PAIR_SR_MINBLOCKS 4
+#endif
 template <int ST, int CORR, int ZC, bool SR>
-__global__ void __launch_bounds__(kBlockThreads, SR ? 4 : LBC_PAIR_MINBLOCKS)
+__global__ void __launch_bounds__(kBlockThreads, SR ? LBC_PAIR_SR_MINBLOCKS : LBC_PAIR_MINBLOCKS)
 k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
             float F2s, const float *__restrict__ ff, unsigned sr_key)
 {
