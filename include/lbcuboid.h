@@ -100,10 +100,10 @@ typedef struct {
                               rounding (hardware cvt.rs, random bits from a counter-based hash
                               of (node, direction, time step, rounding_seed)) */
     unsigned rounding_seed;
-    int kernel;            /* 0: automatic (row-staged kernel for 4-byte storage, two nodes per
-                              thread for 2-byte storage, where the lattice allows it); 1: one
-                              node per thread; 2: two nodes per thread without staging;
-                              3: row-staged for every storage form (cross-checks, measurements) */
+    int kernel;            /* 0: automatic (two nodes per thread where the lattice allows it,
+                              else one node per thread); 1: one node per thread; 2: two nodes
+                              per thread; 3: row-staged through shared memory with bulk copies
+                              (4- and 2-byte storage, rows of up to 1024 nodes) */
     int model;             /* collision model: 0 = central moments (3DCCM, Sec. 3.2), 1 = raw
                               moments with the same corrected equilibria (3DCRM, Sec. 3.2 raw
                               formulation and Sec. 7); model 1 needs LB_CORR_LOCAL and is not

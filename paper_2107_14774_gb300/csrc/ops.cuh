@@ -200,17 +200,16 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
     }
 }
 
-// The staged (bulk-copy) kernel: 4-byte storage (for the 2-byte forms the
-// two-node kernel from global memory measured faster), LOCAL corrections, rows of
+// The staged (bulk-copy) kernel, on request (kernel 3): LOCAL corrections, rows of
 // at most 1024 elements whose byte length is a multiple of 16, no walls normal to
-// x, no moving lid.
+// x, no moving lid.  The automatic choice is the two-node kernel: at five CTAs per
+// SM it measured 98 % of the copy bandwidth on 512-wide FP32 rows against 93 % for
+// this one, and faster for 2-byte storage.
 template <int ST>
 bool Ops<ST>::use_bulk(const LaunchArgs &a)
 {
     if (ST == LB_F64 || a.corr != LB_CORR_LOCAL || a.model != 0 || !a.err) return false;
-    // automatic choice: 4-byte storage on rows of at most 512 nodes (two CTAs per SM);
-    // wider rows leave one CTA of 8 warps per SM, where the two-node kernel measured faster
-    if (a.kernel != 3 && (a.kernel != 0 || sizeof(S) != 4 || a.g.nx > 512)) return false;
+    if (a.kernel != 3) return false;
     const unsigned elem = (unsigned)sizeof(S);
     return a.g.nx >= 2 && a.g.nx <= 1024 && (a.g.nx * elem) % 16 == 0 && !a.g.wall[0] && a.lid_u == 0.0 &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);

@@ -36,8 +36,8 @@ class Lattice:
     storage: "f64", "f32", "f32s" (shifted FP32), "f16s", "bf16s" (shifted FP16 /
     BF16, FP32 arithmetic).  corr: "none", "lowmach", "local", "full".
     walls: any of "x", "y", "z" (half-way bounce-back walls normal to that axis).
-    kernel: "auto" (row-staged or two-node kernel where possible), "one" (one node per thread),
-    "pair" (two nodes per thread, no staging) or "staged" (row-staged for every storage form).
+    kernel: "auto" (two-node kernel where possible), "one" (one node per thread), "pair" (two
+    nodes per thread) or "staged" (rows staged in shared memory by bulk copies).
     rounding: "nearest" or "stochastic" (FP16/BF16 storage only).
     model: "central" (3DCCM) or "raw" (3DCRM: raw moments relaxed with the same corrected
     equilibria; LOCAL corrections only).

@@ -270,9 +270,9 @@ def test_unstable_state_is_reported():
 @pytest.mark.parametrize("walls", ["y", "z", "yz", ""])
 @pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f32s", 1e-5), ("f16s", 1e-3), ("bf16s", 6e-3)])
 def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
-    """The row-staged kernel (auto), the two-nodes-per-thread kernel (packed FP32x2
-    arithmetic) and the one-node kernel agree with the oracle and with each other
-    (channel walls, force field)."""
+    """The row-staged kernel, the two-nodes-per-thread kernel (packed FP32x2 arithmetic;
+    the automatic choice) and the one-node kernel agree with the oracle and with each
+    other (channel walls, force field)."""
     from paper_2107_14774_gb300 import Lattice
     n, r, s = (64, 20, 12), 0.5, 1.0
     rho, u = synth.solenoidal_random(*n, r, s, 3.0, 0.03, seed=21)
