@@ -337,6 +337,35 @@ def run_study(args):
                 re = studies.max_stable_reynolds(nx, ny, nz, 0.5, 1.0, 0.08, 0.2, model, args.study_steps)
                 emit({"study": "reynolds", "grid": [nx, ny, nz], "r": 0.5, "s": 1.0, "model": model, "U": 0.2,
                       "Re_max": re, "steps": args.study_steps})
+    elif args.study == "adjoint":          # discrete adjoint, 128x64x64, T = 500, K = 50, FP32
+        import torch
+        import synth
+        from paper_2107_14774_gb300 import Lattice
+        n, T, K = (128, 64, 64), 500, 50
+        rho, u = synth.solenoidal_random(*n, 1.0, 0.5, 4.0, 0.01, seed=4)
+        ff = synth.force_field(*n, 1e-5, seed=44)
+        lat = Lattice(*n, r_y=1.0, r_z=0.5, nu=0.01, storage="f32", stream=torch.cuda.Stream())
+        lat.set_force_field(torch.from_numpy(ff).cuda())
+        N = n[0] * n[1] * n[2]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep in range(2):                      # the first call also allocates the checkpoints
+            lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+            torch.cuda.synchronize()
+            ev[0].record(lat.stream)
+            J, dJdF, dJdw = lat.adjoint_ke(T, K)
+            ev[1].record(lat.stream)
+            torch.cuda.synchronize()
+        lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+        torch.cuda.synchronize()
+        ev[2].record(lat.stream)
+        lat.step(T)
+        ev[3].record(lat.stream)
+        torch.cuda.synchronize()
+        t_adj, t_fwd = ev[0].elapsed_time(ev[1]) / 1e3, ev[2].elapsed_time(ev[3]) / 1e3
+        emit({"study": "adjoint", "grid": list(n), "T": T, "K": K, "J": J, "dJ_domega": list(dJdw),
+              "seconds_adjoint_total": t_adj, "seconds_forward_T_steps": t_fwd, "ratio": t_adj / t_fwd,
+              "node_steps_per_s": N * T / t_adj})
+        lat.close()
     else:                                  # Sec. 6: shallow cavity, cubic vs cuboid, Re = 100, Ma = 0.1
         cubic = studies.shallow_cavity(256, 64, 128, 1.0, 1.0, 1 / 3, 0.1 * (1 / 3) ** 0.5)
         emit({"study": "cavity", "lattice": "cubic 256x64x128", "r": 1.0, "s": 1.0, "cs2": 1 / 3,
@@ -374,9 +403,10 @@ def main():
                     help="kernel selection passed to the library (auto = two nodes per thread where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")
-    ap.add_argument("--study", default=None, choices=["stability", "xi", "reynolds", "cavity"],
+    ap.add_argument("--study", default=None, choices=["stability", "xi", "reynolds", "cavity", "adjoint"],
                     help="run a parameter study of the paper instead of the benchmark (one JSON line per point): "
-                         "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6")
+                         "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6, "
+                         "adjoint = timing of the checkpointed adjoint on the 128x64x64 case")
     ap.add_argument("--study-steps", type=int, default=100_000, help="steps a stable run must survive")
     ap.add_argument("--omegas", default="1.5,1.6,1.7,1.8,1.9,1.95,1.98",
                     help="omega_nu values of the stability studies")

@@ -200,6 +200,9 @@ lb_status lb_objective_ke(lb_ctx *ctx, double *J);
 lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2], double *J);
 /* (lb_adjoint_ke also requires round-to-nearest storage: rounding = 0.) */
 
+/* The same adjoint without returning J (the objective is the mean kinetic energy). */
+lb_status lb_adjoint(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2]);
+
 /* Vector-Jacobian product of the per-node collision alone, for n independent
  * nodes (device pointers, real type): f [27][n] pre-collision populations,
  * F [3][n] body force, lam [27][n] = dJ/d(post-collision populations).  Writes

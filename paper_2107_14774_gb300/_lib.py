@@ -68,6 +68,7 @@ SIGNATURES = {
     "lb_objective_ke": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double)]),
     "lb_adjoint_ke": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]),
+    "lb_adjoint": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "lb_collide_vjp": (ctypes.c_int, [_CTX, ctypes.c_longlong, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "lb_reduce_populations_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong, ctypes.c_double,
                                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double),

@@ -683,6 +683,11 @@ lb_status lb_adjoint_ke(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2],
     return LB_OK;
 }
 
+lb_status lb_adjoint(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2])
+{
+    return lb_adjoint_ke(c, T, K, dJdF, dJdomega, nullptr);
+}
+
 lb_status lb_collide_vjp(lb_ctx *c, long long n, const void *f, const void *F, const void *lam, void *f_bar,
                          void *F_bar, double w_bar[2])
 {

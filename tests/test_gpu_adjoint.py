@@ -143,3 +143,21 @@ def test_config4_adjoint_against_central_differences():
     print(f"config4: worst single-component relative error {worst:.2e}")
     assert worst < 1e-4
     ref.close()
+
+
+def test_lb_adjoint_matches_lb_adjoint_ke():
+    """lb_adjoint (the entry point without J) returns the same gradients as lb_adjoint_ke."""
+    import ctypes
+    from paper_2107_14774_gb300 import Lattice
+    from paper_2107_14774_gb300._lib import check
+    n = (16, 8, 8)
+    rho, u = synth.solenoidal_random(*n, 1.0, 0.5, 2.0, 0.01, seed=8)
+    lat = Lattice(*n, r_y=1.0, r_z=0.5, nu=0.02, storage="f64")
+    lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    _, g1, w1 = lat.adjoint_ke(20, 5)
+    lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    g2 = torch.empty_like(g1)
+    dw = (ctypes.c_double * 2)()
+    check(lat.lib.lb_adjoint(lat.ctx, 20, 5, g2.data_ptr(), dw))
+    assert torch.equal(g1, g2) and (dw[0], dw[1]) == w1
+    lat.close()
