@@ -430,3 +430,66 @@ def test_graph_replay_is_bit_identical(storage, walls, lid):
         out.append(lat.populations().cpu().numpy())
         lat.close()
     assert np.array_equal(out[0], out[1])
+
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+def test_full_size_config5_sampled_nodes(oracle_mod, storage):
+    """Channel 768x192x384 (config 5: r = 0.25, s = 1, cs2 = 1/48, nu = 0.005, walls normal
+    to y, Poiseuille base flow plus a 5 % perturbation, uniform force), in the launch
+    configuration the bench times, one fused step: for sampled nodes, wall rows included,
+    the stored post-collision values against the oracle's collision of the same stored
+    pre-collision values (pulled from the GPU's initial state by the streaming rule:
+    f_a(x) = S_a(x - e_a) with periodic wrap, S_opp(a)(x) across a y wall).
+    FP32: <= 2e-6 of the node's largest population; BF16: the oracle's output rounded by
+    its storage emulation, within one storage ulp (plus 16 FP32 ulps of w)."""
+    from paper_2107_14774_gb300 import Lattice
+    n, r, s, cs2, nu = (768, 192, 384), 0.25, 1.0, 1 / 48, 0.005
+    rho, u, Fx = synth.channel(*n, r, s, 0.02, nu, 0.05, seed=5)
+    lat = Lattice(*n, r_y=r, r_z=s, nu=nu, cs2=cs2, storage=storage, walls="y", force=(Fx, 0.0, 0.0))
+    assert "k_step_pair" in lat.step_kernel
+    lat.init(torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+    p = lat.params
+    o = oracle_mod.Oracle(r=r, s=s, cs2=cs2, omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
+                          storage_emulation=None if storage == "f32" else storage)
+    e = o.velocities()
+    opp = [int(np.flatnonzero((e == -e[:, [a]]).all(axis=0))[0]) for a in range(27)]
+    w = o.equilibrium(1.0, [0, 0, 0])
+    dt = torch.float32 if storage == "f32" else torch.bfloat16
+    rng = np.random.default_rng(5)
+    pts = [(0, 0, 0), (n[0] - 1, n[1] - 1, n[2] - 1), (100, 0, 17), (5, n[1] - 1, 300)] + [
+        tuple(int(rng.integers(0, m)) for m in n) for _ in range(10)]
+    S0 = lat.get_state().view(dt).reshape((27,) + n[::-1])
+    blocks = {}
+    for (i, j, k) in pts:      # the 3x3x3 neighbourhood of each sampled node in the stored state
+        ks = [(k + d) % n[2] for d in (-1, 0, 1)]
+        js = [(j + d) % n[1] for d in (-1, 0, 1)]
+        is_ = [(i + d) % n[0] for d in (-1, 0, 1)]
+        blocks[(i, j, k)] = S0[:, ks][:, :, js][:, :, :, is_].double().cpu().numpy()
+    del S0
+    lat.step(1)
+    S1 = lat.get_state().view(dt).reshape((27,) + n[::-1])
+    worst = 0.0
+    for (i, j, k) in pts:
+        blk = blocks[(i, j, k)]
+        f = np.empty(27)
+        for a in range(27):
+            if not 0 <= j - e[1, a] < n[1]:
+                f[a] = blk[opp[a], 1, 1, 1]
+            else:
+                f[a] = blk[a, 1 - e[2, a], 1 - e[1, a], 1 - e[0, a]]
+        got = S1[:, k, j, i].double().cpu().numpy()
+        if storage == "f32":
+            want = o.collide_node(f, (Fx, 0.0, 0.0))
+            worst = max(worst, float(np.abs(got - want).max() / np.abs(want).max()))
+        else:
+            ft = o.collide_node(w + f, (Fx, 0.0, 0.0))
+            q = o.quantize(ft.reshape(27, 1, 1, 1)).ravel() - w
+            want = torch.from_numpy(q).to(torch.bfloat16).double().numpy()
+            sp = 2.0 ** (np.frexp(np.where(want == 0, 1e-300, want))[1] - 1 - 7)
+            d = np.abs(got - want) / sp
+            floor = 2.0 ** -20 * w / sp
+            worst = max(worst, float(np.max(d - np.minimum(d, floor))))
+    lat.close()
+    print(storage, "worst", worst)
+    assert worst < (2e-6 if storage == "f32" else 1.0 + 1e-9)
