@@ -172,7 +172,7 @@ class Lattice:
         return np.array(list(out))
 
     def is_stable(self) -> bool:
-        """lb_reduce's verdict: False once a density is non-positive or not finite."""
+        """lb_reduce's status: False once a density is non-positive or not finite."""
         out = (ctypes.c_double * 4)()
         st = self.lib.lb_reduce(self.ctx, out)
         if st == _lib.LB_EUNSTABLE:

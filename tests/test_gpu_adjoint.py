@@ -91,8 +91,8 @@ def test_adjoint_leaves_state_after_T_steps():
     b.close()
 
 
-def test_config4_adjoint_against_central_differences():
-    """Config 4: 128x64x64 periodic, r_z=0.5, FP32, mean kinetic energy after T=500
+def test_adjoint_128x64x64_against_central_differences():
+    """Adjoint case 128x64x64 periodic, r_z=0.5, FP32, mean kinetic energy after T=500
     steps, checkpoint every 50; u0 from the solenoidal generator at u_rms=0.01 (seed 4),
     F i.i.d. N(0, (1e-5)^2) (seed 44).  The FP32 adjoint against central differences
     of the FP64 forward: dJ/domega_nu, dJ/domega_xi (h = 1e-3 relative), the directional
@@ -126,7 +126,7 @@ def test_config4_adjoint_against_central_differences():
     d_wn = (J64(wn0 * (1 + h), wb0, ff) - J64(wn0 * (1 - h), wb0, ff)) / (2 * h * wn0)
     d_wb = (J64(wn0, wb0 * (1 + h), ff) - J64(wn0, wb0 * (1 - h), ff)) / (2 * h * wb0)
     d_v = (J64(wn0, wb0, ff + h * v) - J64(wn0, wb0, ff - h * v)) / (2 * h)
-    print(f"config4: J {J32:.6e} vs {J0:.6e}; dJ/dwn {dJdw[0]:.6e} vs FD {d_wn:.6e}; "
+    print(f"adjoint 128x64x64: J {J32:.6e} vs {J0:.6e}; dJ/dwn {dJdw[0]:.6e} vs FD {d_wn:.6e}; "
           f"dJ/dwb {dJdw[1]:.6e} vs {d_wb:.6e}; <dJ/dF,v> {(dJdF * v).sum():.6e} vs {d_v:.6e}")
     assert dJdw[0] == pytest.approx(d_wn, rel=1e-4)
     assert dJdw[1] == pytest.approx(d_wb, rel=1e-4)
@@ -140,7 +140,7 @@ def test_config4_adjoint_against_central_differences():
         e[c, k, j, i] = eps
         d = (J64(wn0, wb0, ff + e) - J64(wn0, wb0, ff - e)) / (2 * eps)
         worst = max(worst, abs(dJdF[c, k, j, i] - d) / abs(d))
-    print(f"config4: worst single-component relative error {worst:.2e}")
+    print(f"adjoint 128x64x64: worst single-component relative error {worst:.2e}")
     assert worst < 1e-4
     ref.close()
 

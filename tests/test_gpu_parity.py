@@ -72,7 +72,7 @@ def test_fp64_parity_force_field(oracle_mod):
     lat.close()
 
 
-def test_config1_taylor_green_fp64_full_run(oracle_mod):
+def test_taylor_green_32x32x16_fp64_full_run(oracle_mod):
     """32x32x16, r=1, s=0.5, nu=0.01, u0=0.02, FP64, 100 steps: fields within 1e-12 of the
     oracle; mass conserved to 1e-13 and total momentum zero."""
     n, r, s = (32, 32, 16), 1.0, 0.5
@@ -90,8 +90,8 @@ def test_config1_taylor_green_fp64_full_run(oracle_mod):
 
 
 @pytest.mark.parametrize("storage,steps,tol", [("f64", 1000, TOL64), ("f32s", 300, TOL32), ("f32", 300, 1e-4)])
-def test_config2_duct_parity(oracle_mod, storage, steps, tol):
-    """Config 2 as specified: 16x64x128 duct, r=0.5, s=2, walls y/z, periodic x,
+def test_duct_16x64x128_parity(oracle_mod, storage, steps, tol):
+    """The 16x64x128 duct from rest: r=0.5, s=2, walls y/z, periodic x,
     F=(1e-6,0,0), starting from rest.  The flow is invariant along x (periodic x,
     uniform force and initial state), so the GPU field must be identical in every
     x-column and the oracle runs the 1x64x128 cross-section.
@@ -114,12 +114,12 @@ def test_config2_duct_parity(oracle_mod, storage, steps, tol):
                           walls="yz", force=(1e-6, 0.0, 0.0))
     rr, ur = o.moments(o.run(o.init(np.ones((n[2], n[1], 1)), np.zeros((3, n[2], n[1], 1))), steps))
     e_rho, e_u = rel(rg[..., :1], rr), rel(ug[..., :1], ur)
-    print(f"config2 {storage}: rel err rho {e_rho:.2e}  u {e_u:.2e}")
+    print(f"duct {storage}: rel err rho {e_rho:.2e}  u {e_u:.2e}")
     assert e_rho < tol and e_u < tol
 
 
-def test_config2_duct_disturbed_fp64(oracle_mod):
-    """The duct of config 2 with a seeded solenoidal disturbance added to the initial
+def test_duct_16x64x128_disturbed_fp64(oracle_mod):
+    """The 16x64x128 duct with a seeded solenoidal disturbance added to the initial
     state, so that every velocity component and every wall link carries signal."""
     n, r, s, cs2 = (16, 64, 128), 0.5, 2.0, 1 / 12
     rho, up = synth.solenoidal_random(*n, r, s, 3.0, 0.01, seed=2)
@@ -130,7 +130,7 @@ def test_config2_duct_disturbed_fp64(oracle_mod):
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_config2_duct_converges_to_series(storage):
+def test_duct_16x64x128_converges_to_series(storage):
     """Full config-2 run (20k steps) on the GPU against the rectangular-duct series (Eq. 70
     generalised), 2a = ny r = 32, 2b = nz s = 256."""
     from paper_2107_14774_gb300 import Lattice
@@ -161,8 +161,8 @@ def test_reduced_precision_storage_short_run(oracle_mod, storage, tol):
     lat.close()
 
 
-def test_full_size_config3_sampled_nodes(oracle_mod):
-    """512x256x256 (config 3), FP32 storage, one fused step from the seeded solenoidal
+def test_full_size_decaying_512x256x256_sampled_nodes(oracle_mod):
+    """Decaying anisotropic flow 512x256x256, FP32 storage, one fused step from the seeded solenoidal
     field: sampled nodes (and all 27 populations) against the oracle, which computes
     each sampled node's 27 upstream collisions one by one from the same inputs."""
     from paper_2107_14774_gb300 import Lattice
@@ -434,8 +434,8 @@ def test_graph_replay_is_bit_identical(storage, walls, lid):
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16s"])
-def test_full_size_config5_sampled_nodes(oracle_mod, storage):
-    """Channel 768x192x384 (config 5: r = 0.25, s = 1, cs2 = 1/48, nu = 0.005, walls normal
+def test_full_size_channel_768x192x384_sampled_nodes(oracle_mod, storage):
+    """Channel 768x192x384 (r = 0.25, s = 1, cs2 = 1/48, nu = 0.005, walls normal
     to y, Poiseuille base flow plus a 5 % perturbation, uniform force), in the launch
     configuration the bench times, one fused step: for sampled nodes, wall rows included,
     the stored post-collision values against the oracle's collision of the same stored
