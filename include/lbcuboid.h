@@ -203,6 +203,13 @@ lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2
 /* The same adjoint without returning J (the objective is the mean kinetic energy). */
 lb_status lb_adjoint(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2]);
 
+/* Self-test of failure detection without a GPU fault (no counterpart in the paper):
+ * runs one thread that waits, with the bounded mbarrier wait of the row-staged kernel
+ * and a short limit, on a phase nothing completes, then completes it and waits again.
+ * out[0] = 1 if the first wait gave up (as it must), out[1] = 1 if the second
+ * succeeded.  Uses the current device and the legacy default stream; synchronises. */
+lb_status lb_selftest_bounded_wait(int out[2]);
+
 /* Vector-Jacobian product of the per-node collision alone, for n independent
  * nodes (device pointers, real type): f [27][n] pre-collision populations,
  * F [3][n] body force, lam [27][n] = dJ/d(post-collision populations).  Writes

@@ -74,6 +74,7 @@ SIGNATURES = {
                                                       ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                                       ctypes.POINTER(ctypes.c_double), _P]),
     "lb_step_kernel": (ctypes.c_char_p, [_CTX]),
+    "lb_selftest_bounded_wait": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "lb_last_error": (ctypes.c_char_p, []),
 }
 

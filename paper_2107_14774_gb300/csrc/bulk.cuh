@@ -65,9 +65,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 // Bounded wait for the phase with the given parity; false if the limit ran out.
 // Repeated polls back off with a short sleep so that waiting warps leave the
 // issue slots to the warps that are computing.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned limit = kSpinLimit)
 {
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it >= 2) __nanosleep(64);
     }

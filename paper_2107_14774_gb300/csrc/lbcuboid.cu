@@ -136,6 +136,23 @@ unsigned step_key(const lb_ctx *c)
     return x | 1u;
 }
 
+// Self-test of the bounded mbarrier wait of the row-staged kernel: one thread
+// initialises an mbarrier for one arrival and waits for its first phase with a
+// short limit while nothing arrives (the wait must give up and say so), then
+// arrives itself and waits again (the wait must succeed).
+constexpr unsigned kProbeLimit = 1u << 12;
+
+__global__ void k_wait_probe(int *out)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    out[0] = mbar_wait_bounded(&bar, 0u, kProbeLimit) ? 0 : 1;    // nobody arrives: must time out
+    mbar_arrive(&bar);
+    out[1] = mbar_wait_bounded(&bar, 0u, kProbeLimit) ? 1 : 0;    // phase 0 completed
+}
+
 template <class F>
 cudaError_t dispatch(int st, F &&f)
 {
@@ -707,6 +724,22 @@ lb_status lb_collide_vjp(lb_ctx *c, long long n, const void *f, const void *F, c
         return decltype(ops)::collide_vjp(a, f, F, lam, f_bar, F_bar, n, wpart);
     }));
     return sum_pairs(c, wpart, nb, w_bar);
+}
+
+lb_status lb_selftest_bounded_wait(int out[2])
+{
+    if (!out) return fail(LB_EINVAL, "lb_selftest_bounded_wait: null argument");
+    int *d = nullptr;
+    LB_CUDA(cudaMalloc(&d, 2 * sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0xff, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 32>>>(d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    LB_CUDA(e);
+    return LB_OK;
 }
 
 const char *lb_step_kernel(const lb_ctx *c)
