@@ -181,7 +181,11 @@ struct PostState {
 // correctly rounded reciprocal times the numerator (the quantities divided are
 // O(u^2) corrections and the density, well inside the FP32 error budget).
 __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+#ifdef LBC_FAST_DIV
+__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+#else
 __device__ __forceinline__ float div_(float a, float b) { return a * __frcp_rn(b); }
+#endif
 __device__ __forceinline__ F2 div_(F2 a, F2 b) { return F2(div_(a.v.x, b.v.x), div_(a.v.y, b.v.y)); }
 
 // Relaxation of one node (App. D) from its raw moments (V = float/double for one
