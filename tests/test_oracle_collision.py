@@ -246,3 +246,52 @@ def test_corrected_equilibria_cancel_the_truncation_errors(oracle_mod, r, s, cs2
         assert (t7 - (1 - wn) * n7) / wn == pytest.approx(q7, rel=1e-9, abs=1e-15)
         assert (t8 - (1 - wn) * n8) / wn == pytest.approx(q8, rel=1e-9, abs=1e-15)
         assert (t9 - (1 - wb) * n9) / wb == pytest.approx(q9, rel=1e-9, abs=1e-15)
+
+
+def test_full_mode_density_gradient_is_exact_for_quadratics(oracle_mod):
+    """FULL mode takes grad rho from second-order differences of the density field
+    (central inside, one-sided next to a wall; spacings 1, r, s).  Second-order stencils
+    are exact for a quadratic density, so every node of the lattice collision must equal
+    the single-node collision given the analytic gradient (the lambda terms act through
+    u . grad rho, so the velocity is non-zero)."""
+    n, r, s = (6, 5, 7), 0.5, 1.3
+    o = oracle_mod.Oracle(*n, r=r, s=s, cs2=0.06, omega_nu=1.6, omega_xi=1.2, corr=oracle_mod.CORR_FULL,
+                          walls="xyz")
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    X, Y, Z = i * 1.0, j * r, k * s
+    a, b, c, d, e, g = 2e-3, -1e-4, -3e-3, 2e-4, 1.5e-3, 1e-4
+    rho = 1 + a * X + b * X ** 2 + c * Y + d * Y ** 2 + e * Z + g * Z ** 2
+    rng = np.random.default_rng(31)
+    u = 0.03 * rng.standard_normal((3,) + rho.shape)
+    f = o.init(rho, u)
+    ft = o.collide_all(f)
+    changed = 0.0
+    for (kk, jj, ii) in [(0, 0, 0), (n[2] - 1, n[1] - 1, n[0] - 1), (3, 2, 1), (1, 4, 5), (6, 0, 3), (2, 3, 0)]:
+        grad = (a + 2 * b * X[kk, jj, ii], c + 2 * d * Y[kk, jj, ii], e + 2 * g * Z[kk, jj, ii])
+        want = o.collide_node(f[:, kk, jj, ii], grad_rho=grad)
+        np.testing.assert_allclose(ft[:, kk, jj, ii], want, rtol=1e-12, atol=1e-15)
+        changed = max(changed, np.abs(want - o.collide_node(f[:, kk, jj, ii])).max())
+    assert changed > 1e-9       # the gradient terms do act
+
+
+def test_full_mode_density_gradient_wraps_on_periodic_axes(oracle_mod):
+    """On periodic axes the central difference of rho = 1 + A sin(k x) is exactly
+    A cos(k x) sin(k h) / h (wrap included); FULL-mode lattice collisions must equal the
+    single-node collision given that gradient, at the first and last nodes as well."""
+    n, r, s = (8, 6, 10), 0.5, 1.3
+    o = oracle_mod.Oracle(*n, r=r, s=s, cs2=0.06, omega_nu=1.6, omega_xi=1.2, corr=oracle_mod.CORR_FULL)
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    h = (1.0, r, s)
+    kx, ky, kz = (2 * np.pi / (m * hh) for m, hh in zip(n, h))
+    A = (2e-3, -1.5e-3, 1e-3)
+    X, Y, Z = i * h[0], j * h[1], k * h[2]
+    rho = 1 + A[0] * np.sin(kx * X) + A[1] * np.sin(ky * Y) + A[2] * np.sin(kz * Z)
+    rng = np.random.default_rng(32)
+    u = 0.03 * rng.standard_normal((3,) + rho.shape)
+    f = o.init(rho, u)
+    ft = o.collide_all(f)
+    for (kk, jj, ii) in [(0, 0, 0), (n[2] - 1, n[1] - 1, n[0] - 1), (4, 2, 7), (9, 5, 0)]:
+        grad = tuple(a_ * np.cos(kq * q[kk, jj, ii]) * np.sin(kq * hh) / hh
+                     for a_, kq, q, hh in zip(A, (kx, ky, kz), (X, Y, Z), h))
+        np.testing.assert_allclose(ft[:, kk, jj, ii], o.collide_node(f[:, kk, jj, ii], grad_rho=grad),
+                                   rtol=1e-12, atol=1e-15)
