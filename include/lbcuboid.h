@@ -175,12 +175,16 @@ lb_status lb_set_state(lb_ctx *ctx, const void *src, long long time_step);
 /* Number of completed time steps since the last lb_init / lb_set_populations. */
 long long lb_time_step(const lb_ctx *ctx);
 
-/* Replace the uniform body force for the steps enqueued after this call (a
- * time-dependent forcing such as the pulsatile duct of Sec. 5.2 updates it
- * between lb_step calls). */
+/* Replace the uniform body force (Eq. 11c) for the steps enqueued after this call
+ * (a time-dependent forcing such as the pulsatile duct of Sec. 5.2 updates it
+ * between lb_step calls; the step from t to t + 1 uses the force set before it).
+ * force: host array of 3 doubles, read during the call.  LB_EINVAL on a null
+ * pointer or a non-finite component. */
 lb_status lb_set_force(lb_ctx *ctx, const double force[3]);
 
-/* Set the relaxation rates directly, 0 < omega < 2 (instead of nu, zeta). */
+/* Set the relaxation rates of the shear and bulk parts of the second-order moments
+ * directly (App. D; they map to nu and xi through Eq. 53) for the steps enqueued
+ * after this call.  LB_EINVAL unless 0 < omega < 2 for both. */
 lb_status lb_set_rates(lb_ctx *ctx, double omega_nu, double omega_xi);
 
 /* Mean kinetic energy J = (1/N) sum_x rho |u|^2 / 2 of the current populations,
@@ -241,8 +245,8 @@ lb_status lb_reduce_populations_noalloc(const void *f, int real_size, long long 
                                         const double force[3], double out[4], void *stream);
 
 /* Name (with template arguments) of the step kernel lb_step launches for this
- * context, e.g. "k_step_bulk<F32,LOCAL,512,2,2>"; thread-local storage, valid
- * until the next call on the same thread. */
+ * context, e.g. "k_step_pair<F32,LOCAL,1,false>"; thread-local storage, valid
+ * until the next call on the same thread.  No counterpart in the paper. */
 const char *lb_step_kernel(const lb_ctx *ctx);
 
 /* Message of the last error on this thread ("" if none). */
