@@ -47,3 +47,17 @@ def test_single_process_is_its_own_max():
     import bench
     assert bench.allreduce_max(3.5) == 3.5
     assert bench.aggregate_mlups(100, 10, 1, 0.5) == pytest.approx(100 * 10 / 0.5 / 1e6)
+
+
+def test_reference_arm_times_oracle_steps_within_budget():
+    """The reference arm (the oracle on the host cores) sizes its slab so that the run
+    fits the time budget and reports the keys the bench line carries."""
+    import time
+
+    import bench
+    t0 = time.perf_counter()
+    cpu = bench.reference_steps(2, 1, budget_s=2.0)
+    assert time.perf_counter() - t0 < 30.0
+    for key in ("value", "unit", "cores", "kind", "sample", "ms_per_step"):
+        assert key in cpu
+    assert cpu["kind"] == "oracle" and cpu["unit"] == "MLUPS" and cpu["value"] > 0 and cpu["cores"] >= 1
