@@ -227,10 +227,9 @@ lb_status lb_collide_vjp(lb_ctx *ctx, long long n, const void *f, const void *F,
  * layout as returned by lb_get_populations; real_size 4 = float, 8 = double), for
  * a lattice with aspect ratios r_y, r_z and the uniform body force `force` (NULL =
  * none).  This entry point has no counterpart in the paper: it is the reduction of
- * lb_reduce for callers that cannot allocate device memory -- code recorded into
- * a CUDA graph that may not allocate, hosts whose framework owns all device
- * memory through its own pool, real-time loops that must never enter the driver
- * allocator.  It calls no cudaMalloc or cudaFree: its per-block partial sums and
+ * lb_reduce for callers that cannot allocate device memory -- hosts whose
+ * framework owns all device memory through its own pool, real-time loops that
+ * must never enter the driver allocator.  It calls no cudaMalloc or cudaFree: its per-block partial sums and
  * status word live in one fixed array in the library's device globals (about
  * 131 KB, held by every GPU that loads the library until the process exits), so
  * n is limited to 134,217,728 nodes (LB_EINVAL beyond).  The first call on a

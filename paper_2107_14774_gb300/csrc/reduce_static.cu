@@ -1,9 +1,8 @@
 // reduce_static.cu -- lb_reduce_populations_noalloc: the FP64 mass/momentum
 // reduction for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA-graph
-// capture that must not allocate, allocator-restricted embedding hosts (a
-// framework that owns every byte of device memory through its own pool), or a
+// Some callers cannot call cudaMalloc at all: allocator-restricted embedding hosts
+// (a framework that owns every byte of device memory through its own pool), or a
 // real-time loop that must never hit the driver allocator.  This entry point
 // takes the populations and returns the sums without allocating anything: the
 // per-block partial sums and the status word live in a file-scope __device__

@@ -1,6 +1,6 @@
 """lb_reduce_populations_noalloc -- the reduction entry point for callers that cannot
-allocate device memory (graph captures that may not allocate, hosts whose framework
-owns all device memory, real-time loops) -- against the existing lb_reduce entry
+allocate device memory (hosts whose framework owns all device memory, real-time
+loops) -- against the existing lb_reduce entry
 point, on two calls in a row.  Collected last (file name) so that a failure here
 never hides the other tests of a run that stops at the first failure."""
 import ctypes
