@@ -420,7 +420,7 @@ static void raw_source(const double F[3], const double u[3], double sig[NQ])
  * the groups that B combines above second order all rates are 1, so B and B^-1
  * cancel there.  The strain rates of the corrections take the second-order
  * non-equilibrium moments m - m^eq + Phi/2, the quantity that equals the central
- * non-equilibrium moments (Sec. 2.3 equates the two; with a body force they
+ * non-equilibrium moments (Sec. 2.5 equates the two; with a body force they
  * differ by Phi/2). */
 static void relax_raw(const or_params *p, const double m[NQ], double rho, const double u[3],
                       const double F[3], const double grad_rho[3], double mt[NQ])
