@@ -87,7 +87,7 @@ typedef struct {
     double nu;             /* shear viscosity > 0: omega_nu = 1/(nu/cs2 + 1/2) (Eq. 53) */
     double zeta;           /* bulk viscosity > 0: omega_xi = 1/(3 zeta/(2 cs2) + 1/2) (Eq. 53);
                               zeta <= 0 selects omega_xi = 1 */
-    double cs2;            /* squared sound speed; 0 selects min(1, r^2, s^2)/3 (Sec. 2.5);
+    double cs2;            /* squared sound speed; 0 selects min(1, r^2, s^2)/3 (Sec. 2.6);
                               must satisfy 0 < cs2 < min(1, r^2, s^2) */
     int storage;           /* lb_storage */
     int corr;              /* lb_corr */
@@ -105,7 +105,7 @@ typedef struct {
                               per thread; 3: row-staged through shared memory with bulk copies
                               (4- and 2-byte storage, rows of up to 1024 nodes) */
     int model;             /* collision model: 0 = central moments (3DCCM, Sec. 3.2), 1 = raw
-                              moments with the same corrected equilibria (3DCRM, Sec. 3.2 raw
+                              moments with the same corrected equilibria (3DCRM, Sec. 3.1 raw
                               formulation and Sec. 7); model 1 needs LB_CORR_LOCAL and is not
                               differentiated by lb_adjoint_ke / lb_collide_vjp */
 } lb_config;

@@ -15,7 +15,7 @@
  * Two independent forms of the per-node collision are provided:
  *   form 0 ("factored"):     m = P f; m <- S m; m^c = F(u) m; relax (App. D);
  *                            m~ = F(-u) m~^c; m~ <- S^-1 m~; f~ = P^-1 m~
- *                            (Sec. 3.2, Eq. LBEcentralmomentcuboidlattice,
+ *                            (Secs. 3.1-3.2, Eq. LBEcentralmomentcuboidlattice,
  *                            Apps. A-G).  P^-1 is obtained by Gauss-Jordan.
  *   form 1 ("definitional"): k_mnp = sum_a f_a (e_ax-ux)^m (e_ay-uy)^n
  *                            (e_az-uz)^p with the cuboid velocities (Eq. 3a);
@@ -412,7 +412,7 @@ static void raw_source(const double F[3], const double u[3], double sig[NQ])
 }
 
 /* Post-collision raw moments mt of the raw-moment scheme (3DCRM: the cuboid
- * raw-moment formulation of Sec. 3.2, Eq. LBErawmomentcuboidlattice, with the
+ * raw-moment formulation of Sec. 3.1, Eq. LBErawmomentcuboidlattice, with the
  * corrected equilibria of the central scheme, Sec. 7):
  *   mt = m + B^-1 { Lambda (B m^eq - B m) + (I - Lambda/2) B Phi },
  * m^eq from Eq. 10, Phi from Eq. 11, Lambda = omega_nu on the off-diagonal and
@@ -420,7 +420,7 @@ static void raw_source(const double F[3], const double u[3], double sig[NQ])
  * the groups that B combines above second order all rates are 1, so B and B^-1
  * cancel there.  The strain rates of the corrections take the second-order
  * non-equilibrium moments m - m^eq + Phi/2, the quantity that equals the central
- * non-equilibrium moments (Sec. 2.5 equates the two; with a body force they
+ * non-equilibrium moments (Sec. 2.6 equates the two; with a body force they
  * differ by Phi/2). */
 static void relax_raw(const or_params *p, const double m[NQ], double rho, const double u[3],
                       const double F[3], const double grad_rho[3], double mt[NQ])

@@ -298,7 +298,7 @@ __device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const
     o.hFy = half * Fy;
     o.hFz = half * Fz;
     if constexpr (raw_model(CORR)) {
-        // Raw-moment scheme (Sec. 3.2 raw formulation; Sec. 7): relaxing the raw second-
+        // Raw-moment scheme (Sec. 3.1 raw formulation; Sec. 7): relaxing the raw second-
         // order moments with the raw sources of Eq. 11 leaves them above the central
         // scheme's post-collision values by half the raw source moments; the
         // deviations below are taken from the raw equilibria of Eq. 10, and every

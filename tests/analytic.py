@@ -23,7 +23,7 @@ def duct_series(y, z, a, b, F, rho, nu, nterms=201):
 
 
 def raw_equilibria_eq10(rho, u, cs2):
-    """Raw-moment equilibria k'^eq_mnp exactly as printed in Eq. 10 (Sec. 2.2),
+    """Raw-moment equilibria k'^eq_mnp exactly as printed in Eq. 10 (Sec. 2.3),
     keyed by the exponent string 'mnp'."""
     ux, uy, uz = u
     c2, c4, c6 = cs2, cs2 * cs2, cs2 ** 3

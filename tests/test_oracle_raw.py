@@ -1,5 +1,5 @@
 """Pins of the oracle's raw-moment scheme (3DCRM: the cuboid raw-moment formulation of
-Sec. 3.2 with the corrected equilibria of the central scheme, compared in Sec. 7)."""
+Sec. 3.1 with the corrected equilibria of the central scheme, compared in Sec. 7)."""
 import numpy as np
 import pytest
 
@@ -131,7 +131,7 @@ def test_raw_shear_wave_decays_at_eq53_viscosity(oracle_mod, r, s, cs2, nu, n, f
 @pytest.mark.parametrize("corr", ["NONE", "LOCAL", "FULL"])
 def test_raw_and_central_agree_up_to_second_order(oracle_mod, corr):
     """The two schemes relax the same second-order non-equilibrium moments (raw and
-    central ones coincide, Sec. 2.5) with sources that are binomial transforms of each
+    central ones coincide, Sec. 2.6) with sources that are binomial transforms of each
     other (Eq. 11 vs Eq. 11c), so their post-collision raw moments of order <= 2 are
     equal for any state and force; they differ above second order."""
     rng = np.random.default_rng(25)
