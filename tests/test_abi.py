@@ -77,3 +77,39 @@ def test_rates_outside_stability_interval_rejected(lib):
     ctx = ctypes.c_void_p()
     # zeta < 0 selects omega_xi = 1, fine; a negative nu is rejected
     assert lib.lb_create(4, 4, 4, 1.0, 1.0, -0.1, 0.0, ctypes.byref(ctx)) == LB_EINVAL
+
+
+def test_header_compiles_as_c_and_a_c_caller_links(lib, tmp_path):
+    """The boundary is plain C: a C99 program that includes the header, fills a
+    configuration, gets LB_EINVAL for a zero-sized lattice and reads the message,
+    compiles with -Wall -Werror, links against the library and runs (no GPU needed)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2107_14774_gb300.build import LIB
+    src = tmp_path / "caller.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "lbcuboid.h"
+int main(void)
+{
+    lb_config cfg;
+    lb_ctx *ctx = NULL;
+    lb_config_default(&cfg, 0, 8, 8, 0.5, 1.0, 0.01);
+    lb_status st = lb_create_ex(&cfg, &ctx);
+    if (st != LB_EINVAL || ctx != NULL) return 1;
+    const char *msg = lb_last_error();
+    if (!msg || !strstr(msg, "dimensions")) return 2;
+    printf("%d %s\n", (int)st, msg);
+    return 0;
+}
+''')
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-llbcuboid", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.startswith("1 ")
