@@ -295,3 +295,32 @@ def test_full_mode_density_gradient_wraps_on_periodic_axes(oracle_mod):
                      for a_, kq, q, hh in zip(A, (kx, ky, kz), (X, Y, Z), h))
         np.testing.assert_allclose(ft[:, kk, jj, ii], o.collide_node(f[:, kk, jj, ii], grad_rho=grad),
                                    rtol=1e-12, atol=1e-15)
+
+
+def test_random_parameters_conservation_and_two_forms(oracle_mod):
+    """Property test over random lattices and rates (both schemes, every correction mode):
+    mass is conserved, momentum gains F, and the factored and definitional forms agree."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(r=st.floats(0.25, 2.0), s=st.floats(0.25, 2.0), frac=st.floats(0.15, 0.9),
+               wn=st.floats(0.2, 1.95), wb=st.floats(0.2, 1.95), mode=st.sampled_from(MODES),
+               model=st.sampled_from(["central", "raw"]), seed=st.integers(0, 2 ** 31 - 1))
+    def check(r, s, frac, wn, wb, mode, model, seed):
+        cs2 = frac * min(1.0, r * r, s * s)           # positive rest weights need cs2 < min(1, r^2, s^2)
+        kw = dict(r=r, s=s, cs2=cs2, omega_nu=wn, omega_xi=wb, corr=getattr(oracle_mod, "CORR_" + mode), model=model)
+        a = oracle_mod.Oracle(form=0, **kw)
+        b = oracle_mod.Oracle(form=1, **kw)
+        rng = np.random.default_rng(seed)
+        u = 0.05 * rng.standard_normal(3) * np.array([1.0, r, s])
+        f = a.equilibrium(1.0 + 0.02 * rng.standard_normal(), u)
+        f = f * (1.0 + 0.01 * rng.standard_normal(27))
+        F = 1e-4 * rng.standard_normal(3)
+        g = 1e-2 * rng.standard_normal(3)
+        fa, fb = a.collide_node(f, F, g), b.collide_node(f, F, g)
+        np.testing.assert_allclose(fa, fb, rtol=1e-9, atol=1e-13 * np.abs(f).max())
+        e = np.array([[1.0], [r], [s]]) * a.velocities()
+        assert fa.sum() == pytest.approx(f.sum(), rel=1e-13)
+        np.testing.assert_allclose(e @ fa, e @ f + F, rtol=0, atol=1e-13)
+    check()
