@@ -223,10 +223,13 @@ lb_status lb_collide_vjp(lb_ctx *ctx, long long n, const void *f, const void *F,
                          void *F_bar, double w_bar[2]);
 
 /* FP64 sums out[0] = sum rho and out[1..3] = sum rho u (rho u = sum f e + F/2)
- * of n nodes, from pre-collision populations f [27][n] (device memory, natural
- * layout as returned by lb_get_populations; real_size 4 = float, 8 = double), for
- * a lattice with aspect ratios r_y, r_z and the uniform body force `force` (NULL =
- * none).  This entry point has no counterpart in the paper: it is the reduction of
+ * of n nodes, from pre-collision populations f [27][n] (device memory of the
+ * current device or managed memory -- anything else, host memory included, returns
+ * LB_EINVAL before any launch; natural layout as returned by lb_get_populations;
+ * real_size 4 = float, 8 = double), for a lattice with aspect ratios r_y, r_z and
+ * the uniform body force `force` (NULL = none).  A per-node force field
+ * (lb_set_force_field) is not included: with one, the momentum differs from
+ * lb_reduce's by half the summed field.  This entry point has no counterpart in the paper: it is the reduction of
  * lb_reduce for callers that cannot allocate device memory -- hosts whose
  * framework owns all device memory through its own pool, real-time loops that
  * must never enter the driver allocator.  It calls no cudaMalloc or cudaFree: its per-block partial sums and
@@ -234,7 +237,9 @@ lb_status lb_collide_vjp(lb_ctx *ctx, long long n, const void *f, const void *F,
  * 131 KB, held by every GPU that loads the library until the process exits), so
  * n is limited to 134,217,728 nodes (LB_EINVAL beyond).  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  All calls
+ * device current and keeps it for the life of the process (a cudaDeviceReset of that
+ * device makes it stale: do not call this entry point after one); make that first
+ * call before any stream capture.  All calls
  * share the array: calls that overlap on the GPU (other streams, other threads)
  * race and must be serialised by the caller; the array keeps the last call's
  * contents.  Work is issued on `stream` (cudaStream_t, NULL = default stream) and

@@ -113,7 +113,9 @@ lb_status fail(lb_status st, const std::string &msg)
 }
 
 // Device address of the scratch array on the current device, looked up once per
-// device (the array's name is only a host-side stand-in in host code).
+// device (the array's name is only a host-side stand-in in host code).  The cached
+// address belongs to the device's primary context: after cudaDeviceReset on that
+// device it is stale, so the entry point must not be called again in that process.
 lb_status scratch_for_current_device(double **out)
 {
     int dev = 0;
@@ -142,6 +144,21 @@ extern "C" lb_status lb_reduce_populations_noalloc(const void *f, int real_size,
         return fail(LB_EINVAL, "lb_reduce_populations_noalloc: n = " + std::to_string(n) +
                                    " exceeds the maximum of " + std::to_string(kMaxNodes) +
                                    " nodes served by the fixed scratch array");
+    // f must be memory the current device can read: a host or numpy pointer (or
+    // another device's memory) would make the kernel fault, so reject it here,
+    // before anything is launched (cudaPointerGetAttributes allocates nothing)
+    int cur = 0;
+    cudaError_t ae = cudaGetDevice(&cur);
+    if (ae != cudaSuccess) return fail(LB_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ae));
+    cudaPointerAttributes attr;
+    ae = cudaPointerGetAttributes(&attr, f);
+    if (ae != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LB_EINVAL, "lb_reduce_populations_noalloc: f is not a CUDA pointer");
+    }
+    if (attr.type != cudaMemoryTypeManaged && !(attr.type == cudaMemoryTypeDevice && attr.device == cur))
+        return fail(LB_EINVAL, "lb_reduce_populations_noalloc: f must be device memory of the current device "
+                               "or managed memory (host memory is not accepted)");
     double *scratch = nullptr;
     lb_status st = scratch_for_current_device(&scratch);
     if (st) return st;
