@@ -15,13 +15,13 @@
  * Two independent forms of the per-node collision are provided:
  *   form 0 ("factored"):     m = P f; m <- S m; m^c = F(u) m; relax (App. D);
  *                            m~ = F(-u) m~^c; m~ <- S^-1 m~; f~ = P^-1 m~
- *                            (Secs. 3.1-3.2, Eq. LBEcentralmomentcuboidlattice,
+ *                            (Secs. 3.1-3.2, the central-moment update of Sec. 3.1,
  *                            Apps. A-G).  P^-1 is obtained by Gauss-Jordan.
  *   form 1 ("definitional"): k_mnp = sum_a f_a (e_ax-ux)^m (e_ay-uy)^n
  *                            (e_az-uz)^p with the cuboid velocities (Eq. 3a);
  *                            relax (App. D); f~ solves M(u) f~ = k~ by LU.
  * Streaming follows Sec. 3.2 (f_a(x,t+1) = f~_a(x - e_a, t)); walls are the
- * link-wise half-way bounce-back of Sec. 4 (Eq. momentumaugmentedBBscheme),
+ * link-wise half-way bounce-back of Sec. 4 (its momentum-augmented form),
  * with the wall-velocity term of the moving lid when a lid is configured.
  *
  * Readings of points where the paper is silent or garbled (all listed in the
@@ -56,7 +56,7 @@ static const int EY[NQ] = {0,0,0,1,-1,0,0,1,1,-1,-1,0,0,0,0,1,-1,1,-1,1,1,-1,-1,
 static const int EZ[NQ] = {0,0,0,0,0,1,-1,0,0,0,0,1,1,-1,-1,1,1,-1,-1,1,1,1,1,-1,-1,-1,-1};
 
 /* Exponents (m,n,p) of the moments in the order of the raw-moment list m
- * (Sec. 3.1, Eq. rawmomentlist) and of the central-moment list m^c. */
+ * (Sec. 3.1, the list of raw moments) and of the central-moment list m^c. */
 static const int MM[NQ] = {0,1,0,0,1,1,0,2,0,0,1,1,2,0,2,0,1,2,2,0,2,1,1,1,2,2,2};
 static const int MN[NQ] = {0,0,1,0,1,0,1,0,2,0,2,0,1,1,0,2,1,2,0,2,1,2,1,2,1,2,2};
 static const int MP[NQ] = {0,0,0,1,0,1,1,0,0,2,0,2,0,2,1,1,1,0,2,2,1,1,2,2,2,1,2};
@@ -172,7 +172,7 @@ static int g_KI[3][3][3];   /* (m,n,p) -> position in the moment list */
 static int g_OPP[NQ];       /* opposite direction: e_opp = -e */
 
 /* P: moment basis of the cubic lattice, P[j][a] = ex^m ey^n ez^p with the
- * cubic velocities (Eq. momentbasiscubiclattice). */
+ * cubic velocities (Sec. 3.1, the moment basis of the cubic lattice). */
 static void setup(void)
 {
     if (g_ready) return;
@@ -201,7 +201,7 @@ static double binom(int n, int k)
 
 /* Frame transformation F(u): central moments from raw moments by the binomial
  * expansion of (e_x-u_x)^m (e_y-u_y)^n (e_z-u_z)^p (Eq. 3a vs Eq. 3b,
- * Eq. centralmomentrawmomentmappings, App. C):
+ * Sec. 3.1 mapping of raw to central moments, App. C):
  *   k_mnp = sum_{a<=m, b<=n, c<=p} C(m,a) C(n,b) C(p,c)
  *           (-u_x)^(m-a) (-u_y)^(n-b) (-u_z)^(p-c) k'_abc.
  * F(-u) is its inverse (App. E). */
@@ -322,7 +322,7 @@ static void relax_central(const or_params *p, const double k[NQ], double rho, co
     /* every other relaxation rate is unity (App. D) */
     const double w1 = 1.0, w3 = 1.0, w111 = 1.0, w211 = 1.0, w4 = 1.0, w122 = 1.0, w222 = 1.0;
 
-    /* B: combine selected moments (App. D, Eq. combinedprecollisioncentramoments) */
+    /* B: combine selected moments (App. D, combined pre-collision central moments) */
     double k2s = K(2,0,0) + K(0,2,0) + K(0,0,2);
     double k2d1 = K(2,0,0) - K(0,2,0);
     double k2d2 = K(2,0,0) - K(0,0,2);
@@ -412,7 +412,7 @@ static void raw_source(const double F[3], const double u[3], double sig[NQ])
 }
 
 /* Post-collision raw moments mt of the raw-moment scheme (3DCRM: the cuboid
- * raw-moment formulation of Sec. 3.1, Eq. LBErawmomentcuboidlattice, with the
+ * raw-moment formulation of Sec. 3.1 (its raw-moment update), with the
  * corrected equilibria of the central scheme, Sec. 7):
  *   mt = m + B^-1 { Lambda (B m^eq - B m) + (I - Lambda/2) B Phi },
  * m^eq from Eq. 10, Phi from Eq. 11, Lambda = omega_nu on the off-diagonal and
@@ -637,7 +637,7 @@ static int equilibrium_node(const or_params *p, double rho, const double u[3], d
 /* Streaming f_a(x, t+1) = ft_a(x - e_a, t) on the integer lattice (Sec. 3.2);
  * a link whose source lies beyond a wall returns as the reflected population
  * of the same node: f_a(x, t+1) = ft_opp(a)(x, t) - [f^eq_opp(a) - f^eq_a](x_w)
- * (Eq. momentumaugmentedBBscheme; the bracket vanishes at a wall at rest). */
+ * (Sec. 4, momentum-augmented bounce-back; the bracket vanishes at a wall at rest). */
 int or_stream(const or_params *p, const double *ft, double *fout)
 {
     setup();

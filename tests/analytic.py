@@ -71,7 +71,7 @@ def fit_decay_rate(times, amps):
 
 def pulsatile_duct(y, z, t, a, Fm, omega, nu, rho=1.0, nterms=200):
     """Time-periodic flow in the square duct |y|, |z| <= a driven by F = Fm cos(omega t)
-    along x (Sec. 5.2, Eq. pulsatileflowanalyticalsolution): u = Re[U e^{i omega t}],
+    along x (Sec. 5.2, its analytical solution): u = Re[U e^{i omega t}],
     U = Fm/(i omega rho) (1 - V), V = 2 sum_n (-1)^n / p_n [cosh(g_n y/a) cos(p_n z/a)
     + cosh(g_n z/a) cos(p_n y/a)] / cosh(g_n), p_n = (2n+1) pi / 2,
     g_n = sqrt(p_n^2 + i Wo^2), Wo = a sqrt(omega / nu).  Readings of the garbled print:

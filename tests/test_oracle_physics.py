@@ -134,7 +134,7 @@ def test_duct_series_solves_poisson_problem():
 
 
 def test_moving_lid_terms_match_eq69(oracle_mod):
-    """The generic momentum-augmented bounce-back (Eq. momentumaugmentedBBscheme with
+    """The generic momentum-augmented bounce-back (Sec. 4, with
     f^eq = Q^-1 m^eq) reproduces the printed cuboid-lattice terms of Eq. 69."""
     r, s, cs2, rho, U = 0.5, 0.8, 0.04, 1.03, 0.07
     o = oracle_mod.Oracle(r=r, s=s, cs2=cs2)
