@@ -31,16 +31,15 @@ __device__ __forceinline__ RelaxBar<T> relax_node_vjp(const RawMoments<T> &m, co
                                                       const PostState<T> &ob)
 {
     static_assert(CORR != LB_CORR_FULL, "the adjoint covers the local correction modes");
-    const T cs2 = P.cs2;
     // ---- forward recomputation ----
     const T dr = m.dr;
     const T rho = T(1) + dr;
     const T irho = div_(T(1), rho);
     const T qx = m.jx + T(0.5) * Fx, qy = m.jy + T(0.5) * Fy, qz = m.jz + T(0.5) * Fz;
     const T ux = qx * irho, uy = qy * irho, uz = qz * irho;
-    const T n200 = m.pxx - cs2 * dr - rho * ux * ux + ux * Fx;
-    const T n020 = m.pyy - cs2 * dr - rho * uy * uy + uy * Fy;
-    const T n002 = m.pzz - cs2 * dr - rho * uz * uz + uz * Fz;
+    const T n200 = m.pxx - P.cs2ax[0] * dr - rho * ux * ux + ux * Fx;
+    const T n020 = m.pyy - P.cs2ax[1] * dr - rho * uy * uy + uy * Fy;
+    const T n002 = m.pzz - P.cs2ax[2] * dr - rho * uz * uz + uz * Fz;
     const T k110 = m.pxy - rho * ux * uy + T(0.5) * (ux * Fy + uy * Fx);
     const T k101 = m.pxz - rho * ux * uz + T(0.5) * (ux * Fz + uz * Fx);
     const T k011 = m.pyz - rho * uy * uz + T(0.5) * (uy * Fz + uz * Fy);
@@ -178,11 +177,11 @@ __device__ __forceinline__ RelaxBar<T> relax_node_vjp(const RawMoments<T> &m, co
     uy_b += (-rho * ux + T(0.5) * Fx) * k110_b;
     Fy_b += T(0.5) * ux * k110_b;
     Fx_b += T(0.5) * uy * k110_b;
-    // n200 = pxx - cs2 dr - rho ux^2 + ux Fx, etc.
+    // n200 = pxx - cs2x dr - rho ux^2 + ux Fx, etc. (cs2 of each axis' rest weights)
     b.m.pxx = n200_b;
     b.m.pyy = n020_b;
     b.m.pzz = n002_b;
-    T dr_b = ob.dr - cs2 * (n200_b + n020_b + n002_b);
+    T dr_b = ob.dr - (P.cs2ax[0] * n200_b + P.cs2ax[1] * n020_b + P.cs2ax[2] * n002_b);
     rho_b -= ux * ux * n200_b + uy * uy * n020_b + uz * uz * n002_b;
     ux_b += (-T(2) * rho * ux + Fx) * n200_b;
     uy_b += (-T(2) * rho * uy + Fy) * n020_b;

@@ -200,22 +200,25 @@ __device__ __forceinline__ PostState<V> relax_node(const RawMoments<V> &m, const
 {
     using T = typename Scalar<V>::type;
     constexpr int CM = corr_mode(CORR);
-    const V cs2 = V(P.cs2);
     const V half = V(T(0.5));
     const V dr = m.dr;
     const V rho = V(T(1)) + dr;
-    const V irho = div_(V(T(1)), rho);
-    // rho u = sum f e + F/2 (Eq. 12)
-    const V ux = fma_(half, Fx, m.jx) * irho;
-    const V uy = fma_(half, Fy, m.jy) * irho;
-    const V uz = fma_(half, Fz, m.jz) * irho;
+    // rho u = sum f e + F/2 (Eq. 12), with u = q - q dr / rho (q = sum f e + F/2): the
+    // rounding of 1 + dr (2^-24 relative in FP32, of one sign while the density
+    // changes slowly) then only touches the small correction term
+    const V ndr = dr * div_(V(T(-1)), rho);
+    const V qx = fma_(half, Fx, m.jx), qy = fma_(half, Fy, m.jy), qz = fma_(half, Fz, m.jz);
+    const V ux = fma_(qx, ndr, qx);
+    const V uy = fma_(qy, ndr, qy);
+    const V uz = fma_(qz, ndr, qz);
 
     // second-order central moments (App. C), diagonal ones as deviations from cs2 rho:
-    // k_200 - cs2 rho = sum h ex^2 - cs2 (rho - 1) - rho ux^2 + ux Fx, etc.
+    // k_200 - cs2 rho = sum h ex^2 - cs2 (rho - 1) - rho ux^2 + ux Fx, etc., with the
+    // second moment of the rest weights of each axis as cs2
     const V rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-    const V n200 = fma_(ux, Fx - rux, m.pxx - cs2 * dr);
-    const V n020 = fma_(uy, Fy - ruy, m.pyy - cs2 * dr);
-    const V n002 = fma_(uz, Fz - ruz, m.pzz - cs2 * dr);
+    const V n200 = fma_(ux, Fx - rux, m.pxx - V(P.cs2ax[0]) * dr);
+    const V n020 = fma_(uy, Fy - ruy, m.pyy - V(P.cs2ax[1]) * dr);
+    const V n002 = fma_(uz, Fz - ruz, m.pzz - V(P.cs2ax[2]) * dr);
     const V k110 = m.pxy - rux * uy + half * (ux * Fy + uy * Fx);
     const V k101 = m.pxz - rux * uz + half * (ux * Fz + uz * Fx);
     const V k011 = m.pyz - ruy * uz + half * (uy * Fz + uz * Fy);

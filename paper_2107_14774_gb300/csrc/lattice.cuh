@@ -52,11 +52,13 @@ __host__ __device__ constexpr int dir_of(int x, int y, int z)
 // (0 = x with speed 1, 1 = y with speed r, 2 = z with speed s):
 //   ic  = 1/c, ic2 = 1/c^2,
 //   w0  = 1 - cs2/c^2 and wpm = cs2/(2 c^2): the rest weights of the 1-D
-//         three-velocity distribution with moments (1, 0, cs2);
+//         three-velocity distribution with moments (1, 0, cs2), rounded so
+//         that w0 + 2 wpm = 1 holds exactly in T;
+//   cs2ax = 2 wpm c^2: the second moment those rounded weights carry;
 //   an  = 3 cs2 - c^2 (anisotropy factor of Eq. 38-40).
 template <class T>
 struct Phys {
-    T c[3], ic[3], ic2[3], w0[3], wpm[3], an[3];
+    T c[3], ic[3], ic2[3], w0[3], wpm[3], an[3], cs2ax[3];
     T cs2;
     T wn, wb;          // omega_nu, omega_xi
     T tn, tb;          // 1/omega - 1/2
@@ -72,8 +74,25 @@ inline Phys<T> make_phys(double r, double s, double cs2, double wn, double wb)
         p.c[i] = (T)c[i];
         p.ic[i] = (T)(1.0 / c[i]);
         p.ic2[i] = (T)(1.0 / (c[i] * c[i]));
-        p.w0[i] = (T)(1.0 - cs2 / (c[i] * c[i]));
-        p.wpm[i] = (T)(0.5 * cs2 / (c[i] * c[i]));
+        // The equilibrium factor of each axis is phi = w + dphi with sum(dphi) = 0, so
+        // every collision multiplies the mass deviation and the momentum by the sums
+        // w0 + 2 wpm of the other axes.  Rounded independently to FP32 these sums miss
+        // 1 by up to 3e-8 (2/3 + 2 (1/6) rounds to 1 + 2^-25), which compounds into a
+        // steady growth of the velocity amplitude of 6e-8 per step; so the larger of
+        // the two weights is rounded and the other is formed from it exactly (the
+        // subtraction from 1 is exact by Sterbenz's lemma, halving/doubling are exact).
+        const double q = cs2 / (c[i] * c[i]);
+        T w0, wpm;
+        if (q <= 0.5) {
+            w0 = (T)(1.0 - q);
+            wpm = (T(1) - w0) * T(0.5);
+        } else {
+            wpm = (T)(0.5 * q);
+            w0 = T(1) - T(2) * wpm;
+        }
+        p.w0[i] = w0;
+        p.wpm[i] = wpm;
+        p.cs2ax[i] = (T)(2.0 * (double)wpm * c[i] * c[i]);
         p.an[i] = (T)(3.0 * cs2 - c[i] * c[i]);
     }
     p.cs2 = (T)cs2;
