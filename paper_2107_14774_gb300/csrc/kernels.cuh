@@ -139,7 +139,7 @@ struct LoadDir<ST, Q> {
 
 // Pre-collision deviations h_a = f_a(x, t) - w_a of one node, streamed in.
 // With a moving lid the incoming links across it get the momentum-augmented
-// term -[f^eq_opp(a) - f^eq_a](rho_w, U) of Eq. momentumaugmentedBBscheme, with
+// term -[f^eq_opp(a) - f^eq_a](rho_w, U) of Sec. 4, with
 // the wall density taken as the fluid node's density sum_a S_a(x) (mass is
 // conserved by the collision, so this is rho(x, t-1)).
 template <int ST>
@@ -341,8 +341,9 @@ struct DirPtrs {
     S *dst[Q];
 };
 
-// Issue the loads of the two nodes (i0, i0+1) of row j, plane k.
-template <int ST>
+// Issue the loads of the two nodes (i0, i0+1) of row j, plane k.  YZW: the lattice
+// has walls normal to y or z (without them no link is tested for a bounce-back).
+template <int ST, bool YZW>
 __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], const DirPtrs<typename Codec<ST>::S> &ptr,
                                            const Geom &g, int i0, unsigned xm, unsigned xp, const int (&ys)[3],
                                            const bool (&yo)[3], int k)
@@ -361,7 +362,7 @@ __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], c
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
-        if (yo[cy] | zo[cz]) {
+        if (YZW && (yo[cy] | zo[cz])) {
             // half-way bounce-back across a y or z wall: f_a(x) = S_opp(a)(x) for both nodes
             raw[a] = IO::ld2(ptr.src[opp(a)] + self);
         } else {
@@ -383,15 +384,27 @@ __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], c
 // Resident CTAs per SM requested from the compiler.  Five CTAs of 128 threads (at most
 // 102 registers; the compiler takes 96 and spills a few words) hide the load latency
 // better than four at 126 registers: measured on GB300, BF16 storage 35.7 -> 39.8 GLUPS,
-// FP32 on 768-wide rows 25.2 -> 31.4 GLUPS; six CTAs (80 registers) spill too much.
+// FP32 on 768-wide rows with y walls 25.2 -> 31.4 GLUPS; six CTAs (80 registers) spill
+// too much.  Without y/z walls the 4-byte forms issue fewer instructions per load and
+// run best at four CTAs (126 registers, no spill): FP32 30.3 -> 32.1 GLUPS on the
+// 512x256x256 decaying flow, while the 2-byte forms keep five (BF16 45.2 vs 41.9).
 #ifndef LBC_PAIR_MINBLOCKS
 #define LBC_PAIR_MINBLOCKS 5
 #endif
 #ifndef LBC_PAIR_SR_MINBLOCKS
 #define LBC_PAIR_SR_MINBLOCKS 5   // stochastic rounding: 33.8 -> 37.7 GLUPS (BF16) at five
 #endif
-template <int ST, int CORR, int ZC, bool SR>
-__global__ void __launch_bounds__(kBlockThreads, SR ? LBC_PAIR_SR_MINBLOCKS : LBC_PAIR_MINBLOCKS)
+#ifndef LBC_PAIR_WIDE_PERIODIC_MINBLOCKS
+#define LBC_PAIR_WIDE_PERIODIC_MINBLOCKS 4
+#endif
+template <int ST, bool SR, bool YZW>
+constexpr int pair_min_blocks()
+{
+    return SR ? LBC_PAIR_SR_MINBLOCKS
+              : ((sizeof(typename Codec<ST>::S) == 4 && !YZW) ? LBC_PAIR_WIDE_PERIODIC_MINBLOCKS : LBC_PAIR_MINBLOCKS);
+}
+template <int ST, int CORR, int ZC, bool SR, bool YZW>
+__global__ void __launch_bounds__(kBlockThreads, pair_min_blocks<ST, SR, YZW>())
 k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
             float F2s, const float *__restrict__ ff, unsigned sr_key)
 {
@@ -408,12 +421,12 @@ k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
     const unsigned xm = (i0 == 0) ? nx - 1u : (unsigned)i0 - 1u;       // source of ex = +1 for node i0
     const unsigned xp = (i0 + 2 == g.nx) ? 0u : (unsigned)i0 + 2u;     // source of ex = -1 for node i0+1
     typename IO::Raw raw[Q];
-    pair_fetch<ST>(raw, ptr, g, i0, xm, xp, ys, yo, k0);
+    pair_fetch<ST, YZW>(raw, ptr, g, i0, xm, xp, ys, yo, k0);
     for (int k = k0; k < kend; ++k) {
         F2 h[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) h[a] = IO::dec(raw[a], D.w[a], D.iscale[a]);
-        if (k + 1 < kend) pair_fetch<ST>(raw, ptr, g, i0, xm, xp, ys, yo, k + 1);
+        if (k + 1 < kend) pair_fetch<ST, YZW>(raw, ptr, g, i0, xm, xp, ys, yo, k + 1);
         const unsigned self = (unsigned)k * nxy + (unsigned)j * nx + (unsigned)i0;
         F2 Fx(F0), Fy(F1), Fz(F2s);
         if (ff) {

@@ -145,6 +145,7 @@ bool Ops<ST>::use_pair(const LaunchArgs &a)
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
 
+#ifndef LBC_OPS_SKIP_PAIR   // defined in the step_*_pair.cu translation units
 template <int ST>
 cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
 {
@@ -170,35 +171,42 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
         switch (a.corr) {
         case LB_CORR_NONE:
             if (sr)
-                k_step_pair<ST, LB_CORR_NONE, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_NONE, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
                                                                                       a.sr_key);
             else
-                k_step_pair<ST, LB_CORR_NONE, ZC, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_NONE, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
                                                                                        0u);
             break;
         case LB_CORR_LOWMACH:
             if (sr)
-                k_step_pair<ST, LB_CORR_LOWMACH, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
+                k_step_pair<ST, LB_CORR_LOWMACH, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
                                                                                          ff, a.sr_key);
             else
-                k_step_pair<ST, LB_CORR_LOWMACH, ZC, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
+                k_step_pair<ST, LB_CORR_LOWMACH, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
                                                                                           ff, 0u);
             break;
         default:
             if (a.model == 1)
-                k_step_pair<ST, LB_CORR_LOCAL | kRawModel, ZC, false><<<grid, block, 0, a.stream>>>(
+                k_step_pair<ST, LB_CORR_LOCAL | kRawModel, ZC, false, true><<<grid, block, 0, a.stream>>>(
                     ptr, a.g, P, D, F0, F1, F2, ff, 0u);
+            else if (!a.g.wall[1] && !a.g.wall[2] && sr)     // periodic in y and z: no bounce-back tests
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, true, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
+                                                                                              F2, ff, a.sr_key);
+            else if (!a.g.wall[1] && !a.g.wall[2])
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, false, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
+                                                                                               F2, ff, 0u);
             else if (sr)
-                k_step_pair<ST, LB_CORR_LOCAL, ZC, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
                                                                                        a.sr_key);
             else
-                k_step_pair<ST, LB_CORR_LOCAL, ZC, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
                                                                                         0u);
             break;
         }
         return cudaGetLastError();
     }
 }
+#endif  // LBC_OPS_SKIP_PAIR
 
 // The staged (bulk-copy) kernel, on request (kernel 3): LOCAL corrections, rows of
 // at most 1024 elements whose byte length is a multiple of 16, no walls normal to
@@ -295,6 +303,7 @@ cudaError_t Ops<ST>::reduce_partial(const LaunchArgs &a, const void *src, double
     return cudaGetLastError();
 }
 
+#ifndef LBC_OPS_SKIP_ADJOINT   // defined in the step_*_adjoint.cu translation units
 template <int ST>
 cudaError_t Ops<ST>::adjoint_seed(const LaunchArgs &a, const void *src, void *lam, void *dJdF, double *jpart)
 {
@@ -363,6 +372,7 @@ cudaError_t Ops<ST>::collide_vjp(const LaunchArgs &a, const void *f, const void 
     }
     return cudaGetLastError();
 }
+#endif  // LBC_OPS_SKIP_ADJOINT
 
 // Name of the kernel that step() launches for these arguments (the same
 // decision as step(), spelled with the template arguments).
@@ -399,9 +409,10 @@ const char *Ops<ST>::step_kernel_name(const LaunchArgs &a)
         snprintf(buf, sizeof(buf), "k_step_bulk<%s,%s,%d,%d,%d>", storage_name(ST), corr_name(a.corr), nxmax, ns,
                  minb);
     } else if (use_pair(a)) {
-        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s%s,%d,%s>", storage_name(ST), corr_name(a.corr),
+        const bool yzw = a.g.wall[1] || a.g.wall[2] || a.model == 1 || a.corr != LB_CORR_LOCAL;
+        snprintf(buf, sizeof(buf), "k_step_pair<%s,%s%s,%d,%s,%s>", storage_name(ST), corr_name(a.corr),
                  a.model == 1 ? "|RAW" : "", kPairPlanes,
-                 (a.sr_key != 0 && sizeof(S) == 2) ? "true" : "false");
+                 (a.sr_key != 0 && sizeof(S) == 2) ? "true" : "false", yzw ? "walls" : "periodic");
     } else {
         snprintf(buf, sizeof(buf), "k_step<%s,%s%s>", storage_name(ST), corr_name(a.corr),
                  a.model == 1 ? "|RAW" : "");
