@@ -108,6 +108,17 @@ typedef struct {
                               moments with the same corrected equilibria (3DCRM, Sec. 3.1 raw
                               formulation and Sec. 7); model 1 needs LB_CORR_LOCAL and is not
                               differentiated by lb_adjoint_ke / lb_collide_vjp */
+    int subdomains;        /* 0 or 1: one domain.  P in 2..16 (and <= nz): lb_step updates the
+                              lattice as P slabs along z, each with one ghost plane on either
+                              side, exchanging after every step the 9 populations with e_z = +1
+                              (-1) of a slab's last (first) plane with the next (previous)
+                              slab through device memory while the slab interiors update on
+                              a second stream -- the slab decomposition a multi-GPU run
+                              distributes, on one device; results are bit-identical to one
+                              domain.  Needs z periodic, corrections other than FULL, no
+                              per-node force field and kernel != 3 (LB_EINVAL otherwise).
+                              Every lb_step call copies the state into the slabs and back
+                              (two extra state copies per call, not per step). */
 } lb_config;
 
 /* Fill *cfg with defaults: FP32 storage, LOCAL corrections, periodic, no

@@ -35,7 +35,7 @@ class lb_config(ctypes.Structure):
         ("storage", ctypes.c_int), ("corr", ctypes.c_int), ("wall_mask", ctypes.c_uint),
         ("force", ctypes.c_double * 3), ("lid_u", ctypes.c_double), ("stream", ctypes.c_void_p),
         ("rounding", ctypes.c_int), ("rounding_seed", ctypes.c_uint), ("kernel", ctypes.c_int),
-        ("model", ctypes.c_int),
+        ("model", ctypes.c_int), ("subdomains", ctypes.c_int),
     ]
 
 

@@ -387,11 +387,11 @@ __device__ __forceinline__ NodeMacro<T> collide(T (&h)[Q], const Phys<T> &P, T F
 // Two collisions (two nodes in the lanes of F2), in place.  The linear transforms
 // run in packed FP32x2 instructions; the per-node relaxation runs per lane.
 template <int CORR, class Out>
-__device__ __forceinline__ void collide_pair(const F2 (&h)[Q], Out &&out, const Phys<float> &P, F2 F0, F2 F1, F2 F2_)
+__device__ __forceinline__ void collide_pair(const F2 (&h)[Q], Out &&out, const Phys<float> &P, F2 F0, F2 F1, F2 F2_,
+                                             F2 grx = F2(0.f), F2 gry = F2(0.f), F2 grz = F2(0.f))
 {
     const RawMoments<F2> m = raw_moments(h, P);
-    const F2 z(0.f);
-    const PostState<F2> o = relax_node<F2, CORR>(m, P, F0, F1, F2_, z, z, z);
+    const PostState<F2> o = relax_node<F2, CORR>(m, P, F0, F1, F2_, grx, gry, grz);
     back_transform_to<raw_model(CORR)>(out, o, P);
 }
 

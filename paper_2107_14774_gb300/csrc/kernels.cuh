@@ -180,7 +180,7 @@ k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__r
     using T = typename C::T;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k = g.kz0 + (int)blockIdx.z * g.kzs;
     if (i >= g.nx || j >= g.ny) return;
     const long long N = g.N;
     const Pull q = make_pull(g, i, j, k);
@@ -232,7 +232,8 @@ k_step(const typename Codec<ST>::S *__restrict__ src, typename Codec<ST>::S *__r
     collide<T, CORR>(h, P, Fx, Fy, Fz, grx, gry, grz);
     if (ST == LB_F16_SHIFTED || ST == LB_BF16_SHIFTED) {
         if (sr_key) {
-            unsigned rs = hash32((unsigned)q.base * 0x9e3779b1u + sr_key) | 1u;
+            const unsigned gbase = (unsigned)q.base + (unsigned)g.zofs * (unsigned)g.nx * (unsigned)g.ny;
+            unsigned rs = hash32(gbase * 0x9e3779b1u + sr_key) | 1u;
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 const unsigned r = xorshift32(rs);
@@ -378,6 +379,62 @@ __device__ __forceinline__ void pair_fetch(typename PairIO<ST>::Raw (&raw)[Q], c
     }
 }
 
+// Density gradient along y or z of the two nodes at `self` (index of the first) from
+// the density field: second-order central differences (periodic wrap), one-sided
+// second-order differences next to a wall, first order if the axis has two nodes
+// (c: the nodes' coordinate on the axis, n its extent, st its stride, ih = 1/spacing).
+__device__ __forceinline__ F2 ld_rho2(const float *rf, unsigned i)
+{
+    return F2(__ldg(reinterpret_cast<const float2 *>(rf + i)));
+}
+__device__ __forceinline__ F2 grad_pair_axis(const float *__restrict__ rf, unsigned self, unsigned st, int c, int n,
+                                             int wall, float ih)
+{
+    if (n == 1) return F2(0.f);
+    if (!wall) {
+        const unsigned p = (c == n - 1) ? self - (unsigned)(n - 1) * st : self + st;
+        const unsigned m = (c == 0) ? self + (unsigned)(n - 1) * st : self - st;
+        return (ld_rho2(rf, p) - ld_rho2(rf, m)) * F2(0.5f * ih);
+    }
+    if (n == 2)
+        return (c == 0 ? ld_rho2(rf, self + st) - ld_rho2(rf, self) : ld_rho2(rf, self) - ld_rho2(rf, self - st)) *
+               F2(ih);
+    if (c == 0)
+        return (F2(-3.f) * ld_rho2(rf, self) + F2(4.f) * ld_rho2(rf, self + st) - ld_rho2(rf, self + 2u * st)) *
+               F2(0.5f * ih);
+    if (c == n - 1)
+        return (F2(3.f) * ld_rho2(rf, self) - F2(4.f) * ld_rho2(rf, self - st) + ld_rho2(rf, self - 2u * st)) *
+               F2(0.5f * ih);
+    return (ld_rho2(rf, self + st) - ld_rho2(rf, self - st)) * F2(0.5f * ih);
+}
+
+// Density pre-pass of LB_CORR_FULL for the two-node kernel: the pre-collision density
+// of the nodes (i0, i0+1), pulled with the same loads as the step (sum of the 27
+// deviations in direction order, as in k_density).
+template <int ST, bool YZW>
+__global__ void __launch_bounds__(kBlockThreads)
+k_density_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, DirConst<float> D, float *__restrict__ rho)
+{
+    using IO = PairIO<ST>;
+    const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = g.kz0 + (int)blockIdx.z * g.kzs;
+    if (i0 >= g.nx || j >= g.ny) return;
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    int ys[3];
+    bool yo[3];
+    axis_sources(j, g.ny, g.wall[1], ys, yo);
+    const unsigned xm = (i0 == 0) ? nx - 1u : (unsigned)i0 - 1u;
+    const unsigned xp = (i0 + 2 == g.nx) ? 0u : (unsigned)i0 + 2u;
+    typename IO::Raw raw[Q];
+    pair_fetch<ST, YZW>(raw, ptr, g, i0, xm, xp, ys, yo, k);
+    F2 s(0.f);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s += IO::dec(raw[a], D.w[a], D.iscale[a]);
+    const unsigned self = (unsigned)k * nxy + (unsigned)j * nx + (unsigned)i0;
+    *reinterpret_cast<float2 *>(rho + self) = (F2(1.f) + s).v;
+}
+
 // ZC consecutive planes per thread: the loads of plane k+1 are issued before the
 // collision of plane k, so that every warp keeps memory requests in flight while
 // it computes (software pipelining across z).
@@ -406,14 +463,14 @@ constexpr int pair_min_blocks()
 template <int ST, int CORR, int ZC, bool SR, bool YZW>
 __global__ void __launch_bounds__(kBlockThreads, pair_min_blocks<ST, SR, YZW>())
 k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
-            float F2s, const float *__restrict__ ff, unsigned sr_key)
+            float F2s, const float *__restrict__ ff, const float *__restrict__ rf, unsigned sr_key)
 {
     using IO = PairIO<ST>;
     const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = blockIdx.z * ZC;
+    const int k0 = g.kz0 + (int)blockIdx.z * ZC * g.kzs;
     if (i0 >= g.nx || j >= g.ny) return;
-    const int kend = min(k0 + ZC, g.nz);
+    const int kend = ZC == 1 ? k0 + 1 : min(k0 + ZC, g.kz1);   // the grid covers exactly the planes
     const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
     int ys[3];
     bool yo[3];
@@ -435,14 +492,24 @@ k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
             Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
             Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
         }
+        F2 grx(0.f), gry(0.f), grz(0.f);
+        if constexpr (corr_mode(CORR) == LB_CORR_FULL) {
+            // density gradient of both nodes from the density pre-pass (the same
+            // stencils as the one-node kernel; x is periodic in this kernel)
+            const unsigned row = self - (unsigned)i0;
+            const F2 rc(__ldg(reinterpret_cast<const float2 *>(rf + self)));
+            grx = F2(rc.v.y - __ldg(rf + row + xm), __ldg(rf + row + xp) - rc.v.x) * F2(0.5f * P.ic[0]);
+            gry = grad_pair_axis(rf, self, nx, j, g.ny, g.wall[1], P.ic[1]);
+            grz = grad_pair_axis(rf, self, nxy, k, g.nz, g.wall[2], P.ic[2]);
+        }
         if constexpr (SR) {
-            unsigned rs = hash32(self * 0x9e3779b1u + sr_key) | 1u;
+            unsigned rs = hash32((self + (unsigned)g.zofs * nxy) * 0x9e3779b1u + sr_key) | 1u;
             collide_pair<CORR>(
                 h, [&](int a, F2 v) { IO::st2sr(ptr.dst[a] + self, v, D.w[a], D.scale[a], xorshift32(rs)); }, P, Fx,
-                Fy, Fz);
+                Fy, Fz, grx, gry, grz);
         } else {
             collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy,
-                               Fz);
+                               Fz, grx, gry, grz);
         }
     }
 }

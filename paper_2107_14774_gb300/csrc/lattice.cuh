@@ -157,11 +157,17 @@ struct DirConst {
     float iscale[Q];
 };
 
-// Grid geometry: extents, wall flags and the stride of each axis.
+// Grid geometry: extents, wall flags and the stride of each axis.  A step launch
+// updates the z-planes kz0, kz0 + kzs, ... below kz1 (all planes: 0, 1, nz); zofs
+// is the global z index of plane 0, which differs from 0 only in a sub-domain (a
+// z-slab with ghost planes) and enters only the stochastic-rounding draws, so that a
+// decomposed run draws the same bits as the whole lattice.
 struct Geom {
     int nx, ny, nz;
     int wall[3];       // 1 = half-way bounce-back walls normal to that axis
     long long N;       // nx * ny * nz
+    int kz0, kz1, kzs; // planes updated by a step launch
+    int zofs;          // global z of plane 0
 };
 
 }  // namespace lbc

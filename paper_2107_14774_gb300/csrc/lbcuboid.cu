@@ -55,6 +55,8 @@ size_t storage_bytes(int st)
     }
 }
 
+constexpr int kMaxSub = 16;   // most z-slabs of a decomposed lattice
+
 }  // namespace
 
 struct lb_ctx {
@@ -88,6 +90,15 @@ struct lb_ctx {
     cudaGraphExec_t graph[2];
     LaunchArgs graph_key[2];
     bool graph_off;
+    // z-slab decomposition (cfg.subdomains > 1): slab p owns the global planes
+    // sub_z0[p] .. sub_z0[p + 1] - 1, stored at its local planes 1 .. n_p between the
+    // ghost planes 0 and n_p + 1; two buffers per slab with the parity of buf
+    int nsub;
+    int sub_z0[kMaxSub + 1];
+    void *sub_buf[2][kMaxSub];
+    int sub_kernel;               // step kernel of the whole lattice (1 or 2), used by every slab
+    cudaStream_t side;            // boundary planes and halo exchange, beside the interiors
+    cudaEvent_t ev_fork, ev_join;
 };
 
 namespace {
@@ -165,6 +176,205 @@ cudaError_t dispatch(int st, F &&f)
     }
 }
 
+// ---------------------------------------------------------------------------
+// z-slab decomposition.  Copies move whole planes as words of W bytes (the largest
+// of 16, 8, 4, 2 that divides a plane's bytes; plane starts are then aligned).
+
+// Between the whole lattice and slab `slab` for every direction (grid z): to the
+// slab, local planes 0 .. n_p + 1 from global planes z0 - 1 .. z0 + n_p (periodic in
+// z); from the slab, its owned planes 1 .. n_p.
+template <class W>
+__global__ void k_slab_copy(W *whole, W *slab, long long nw_whole, long long nw_slab, long long plane_w, int z0,
+                            int nz, int to_slab)
+{
+    const int a = blockIdx.z;
+    const int lp = (int)blockIdx.y + (to_slab ? 0 : 1);
+    int gz = z0 + lp - 1;
+    if (gz < 0) gz += nz;
+    if (gz >= nz) gz -= nz;
+    W *pw = whole + a * nw_whole + gz * plane_w;
+    W *ps = slab + a * nw_slab + lp * plane_w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane_w;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (to_slab)
+            ps[i] = pw[i];
+        else
+            pw[i] = ps[i];
+    }
+}
+
+// Halo exchange after a step, on the buffers just written.  Block z = 18 p + d:
+// d < 9, the d-th direction with e_z = +1: the last owned plane of slab p goes to the
+// lower ghost plane of slab p + 1; d >= 9, a direction with e_z = -1: the first owned
+// plane of slab p goes to the upper ghost plane of slab p - 1 (periodic in p).
+struct SlabSet {
+    void *base[kMaxSub];
+    long long nw[kMaxSub];        // words of one direction array of each slab
+    int np[kMaxSub];              // owned planes of each slab
+    int dir[18];
+    int P;
+    long long plane_w;            // words of one plane
+};
+
+template <class W>
+__global__ void k_halo(SlabSet s)
+{
+    const int p = (int)blockIdx.z / 18, d = (int)blockIdx.z % 18;
+    const int a = s.dir[d];
+    int q, sp, dp;
+    if (d < 9) {
+        q = (p + 1) % s.P;
+        sp = s.np[p];
+        dp = 0;
+    } else {
+        q = (p + s.P - 1) % s.P;
+        sp = 1;
+        dp = s.np[q] + 1;
+    }
+    const W *src = static_cast<const W *>(s.base[p]) + a * s.nw[p] + sp * s.plane_w;
+    W *dst = static_cast<W *>(s.base[q]) + a * s.nw[q] + dp * s.plane_w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < s.plane_w;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// Word size for moving planes of `plane_bytes` bytes.
+int plane_word(size_t plane_bytes)
+{
+    for (int w : {16, 8, 4})
+        if (plane_bytes % w == 0) return w;
+    return 2;
+}
+
+template <class F>
+cudaError_t with_word(int w, F &&f)
+{
+    switch (w) {
+    case 16: return f(uint4());
+    case 8: return f(uint2());
+    case 4: return f(0u);
+    default: return f((unsigned short)0);
+    }
+}
+
+// Launch arguments of slab p: its local geometry (owned planes between two ghost
+// planes, z periodic across the ghosts), and the planes to update: the first and the
+// last owned plane (boundary) or those between them (interior).
+LaunchArgs slab_args(const lb_ctx *c, const LaunchArgs &a, int p, bool boundary)
+{
+    LaunchArgs b = a;
+    const int np = c->sub_z0[p + 1] - c->sub_z0[p];
+    b.g.nz = np + 2;
+    b.g.N = (long long)c->g.nx * c->g.ny * (np + 2);
+    b.g.zofs = c->sub_z0[p] - 1;
+    if (boundary) {
+        b.g.kz0 = 1;
+        b.g.kz1 = np + 1;
+        b.g.kzs = np > 1 ? np - 1 : 1;
+    } else {
+        b.g.kz0 = 2;
+        b.g.kz1 = np;
+        b.g.kzs = 1;
+    }
+    b.kernel = c->sub_kernel;
+    return b;
+}
+
+// Whole lattice <-> slabs (parity p) on the main stream.
+cudaError_t slab_transfer(lb_ctx *c, int p, bool to_slab)
+{
+    const long long plane = (long long)c->g.nx * c->g.ny;
+    const size_t plane_bytes = (size_t)plane * c->sbytes;
+    return with_word(plane_word(plane_bytes), [&](auto word) {
+        using W = decltype(word);
+        const long long plane_w = (long long)(plane_bytes / sizeof(W));
+        for (int s = 0; s < c->nsub; ++s) {
+            const int np = c->sub_z0[s + 1] - c->sub_z0[s];
+            const dim3 grid((unsigned)std::min<long long>((plane_w + 255) / 256, 64), to_slab ? np + 2 : np, Q);
+            k_slab_copy<W><<<grid, 256, 0, c->stream>>>(static_cast<W *>(c->buf[p]), static_cast<W *>(c->sub_buf[p][s]),
+                                                        plane_w * c->g.nz, plane_w * (np + 2), plane_w, c->sub_z0[s],
+                                                        c->g.nz, to_slab ? 1 : 0);
+        }
+        return cudaGetLastError();
+    });
+}
+
+// One time step of the decomposed lattice from slab parity p to p ^ 1: the side stream
+// updates every slab's boundary planes and then exchanges the halos while the main
+// stream updates the interiors; the main stream then waits for the side stream.
+cudaError_t slab_step(lb_ctx *c, const LaunchArgs &a, int p)
+{
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    for (int s = 0; s < c->nsub && e == cudaSuccess; ++s) {
+        LaunchArgs b = slab_args(c, a, s, true);
+        b.stream = c->side;
+        const void *src = c->sub_buf[p][s];
+        void *dst = c->sub_buf[p ^ 1][s];
+        e = dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(b, src, dst); });
+    }
+    if (e == cudaSuccess) {
+        SlabSet set;
+        std::memset(&set, 0, sizeof(set));
+        const size_t plane_bytes = (size_t)c->g.nx * c->g.ny * c->sbytes;
+        const int word = plane_word(plane_bytes);
+        set.P = c->nsub;
+        set.plane_w = (long long)(plane_bytes / word);
+        int nu = 0, nd = 9;
+        for (int q = 0; q < Q; ++q) {
+            if (ez(q) == 1) set.dir[nu++] = q;
+            if (ez(q) == -1) set.dir[nd++] = q;
+        }
+        for (int s = 0; s < c->nsub; ++s) {
+            set.np[s] = c->sub_z0[s + 1] - c->sub_z0[s];
+            set.base[s] = c->sub_buf[p ^ 1][s];
+            set.nw[s] = set.plane_w * (set.np[s] + 2);
+        }
+        e = with_word(word, [&](auto w) {
+            using W = decltype(w);
+            const dim3 grid((unsigned)std::min<long long>((set.plane_w + 255) / 256, 32), 1, 18 * c->nsub);
+            k_halo<W><<<grid, 256, 0, c->side>>>(set);
+            return cudaGetLastError();
+        });
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+    for (int s = 0; s < c->nsub && e == cudaSuccess; ++s) {
+        if (c->sub_z0[s + 1] - c->sub_z0[s] < 3) continue;
+        const LaunchArgs b = slab_args(c, a, s, false);
+        const void *src = c->sub_buf[p][s];
+        void *dst = c->sub_buf[p ^ 1][s];
+        e = dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(b, src, dst); });
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    return e;
+}
+
+// One time step from buffer parity p (whole lattice or slabs).
+cudaError_t one_step(lb_ctx *c, const LaunchArgs &a, int p)
+{
+    if (c->nsub > 1) return slab_step(c, a, p);
+    const void *src = c->buf[p];
+    void *dst = c->buf[p ^ 1];
+    return dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); });
+}
+
+// Slab buffers, the side stream and its events, made on the first decomposed step.
+lb_status ensure_slabs(lb_ctx *c)
+{
+    if (c->side) return LB_OK;
+    for (int s = 0; s < c->nsub; ++s) {
+        const size_t bytes = (size_t)Q * c->g.nx * c->g.ny * (c->sub_z0[s + 1] - c->sub_z0[s] + 2) * c->sbytes;
+        for (int p = 0; p < 2; ++p) {
+            LB_CUDA(cudaMalloc(&c->sub_buf[p][s], bytes));
+            LB_CUDA(cudaMemsetAsync(c->sub_buf[p][s], 0, bytes, c->stream));
+        }
+    }
+    LB_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    LB_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    LB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    return LB_OK;
+}
+
 // Steps per CUDA graph.  On small lattices one step takes less time than a kernel
 // launch, so lb_step replays a captured run of kGraphSteps launches (an even number:
 // the ping-pong buffers end where they started) while the launch arguments stay the
@@ -194,9 +404,7 @@ cudaGraphExec_t graph_for(lb_ctx *c, const LaunchArgs &a)
     cudaError_t e = cudaSuccess;
     int cur = p;
     for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
-        const void *src = c->buf[cur];
-        void *dst = c->buf[cur ^ 1];
-        e = dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); });
+        e = one_step(c, a, cur);
         cur ^= 1;
     }
     cudaGraph_t g = nullptr;
@@ -311,6 +519,14 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (!(wn > 0.0 && wn < 2.0) || !(wb > 0.0 && wb < 2.0))
         return fail(LB_EINVAL, "lb_create_ex: relaxation rates must lie in (0, 2)");
     const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    const int nsub = cfg->subdomains > 1 ? cfg->subdomains : 1;
+    if (nsub > 1) {
+        if (nsub > kMaxSub || nsub > cfg->nz)
+            return fail(LB_EINVAL, "lb_create_ex: subdomains must lie in 1..16 and not exceed nz");
+        if ((cfg->wall_mask & LB_WALL_Z) || cfg->corr == LB_CORR_FULL || cfg->kernel == 3)
+            return fail(LB_EINVAL, "lb_create_ex: subdomains need z periodic, corrections other than FULL and "
+                                   "a kernel other than the row-staged one");
+    }
 
     lb_ctx *c = new lb_ctx();
     std::memset(static_cast<void *>(c), 0, sizeof(*c));
@@ -324,6 +540,12 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     c->g.nz = cfg->nz;
     for (int i = 0; i < 3; ++i) c->g.wall[i] = (cfg->wall_mask >> i) & 1u;
     c->g.N = N;
+    c->g.kz0 = 0;
+    c->g.kz1 = cfg->nz;
+    c->g.kzs = 1;
+    c->g.zofs = 0;
+    c->nsub = nsub;
+    for (int s = 0; s <= nsub; ++s) c->sub_z0[s] = (int)((long long)cfg->nz * s / nsub);
     c->stream = static_cast<cudaStream_t>(cfg->stream);
     c->sbytes = storage_bytes(cfg->storage);
     c->rbytes = cfg->storage == LB_F64 ? 8 : 4;
@@ -350,6 +572,19 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
     }
     if (e == cudaSuccess && cfg->corr == LB_CORR_FULL) e = cudaMalloc(&c->rho_field, N * c->rbytes);
+    if (e == cudaSuccess && nsub > 1) {
+        // every slab runs the kernel the whole lattice would (bit-identical results)
+        const LaunchArgs a = launch_args(c);
+        bool pair = false;
+        switch (cfg->storage) {
+        case LB_F64: pair = Ops<LB_F64>::use_pair(a); break;
+        case LB_F32: pair = Ops<LB_F32>::use_pair(a); break;
+        case LB_F32_SHIFTED: pair = Ops<LB_F32_SHIFTED>::use_pair(a); break;
+        case LB_F16_SHIFTED: pair = Ops<LB_F16_SHIFTED>::use_pair(a); break;
+        default: pair = Ops<LB_BF16_SHIFTED>::use_pair(a); break;
+        }
+        c->sub_kernel = pair ? 2 : 1;
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, bytes, c->stream);
     if (e != cudaSuccess) {
@@ -375,6 +610,11 @@ void lb_destroy(lb_ctx *c)
     cudaFree(c->err);
     drop_graph(c, 0);
     drop_graph(c, 1);
+    for (int s = 0; s < kMaxSub; ++s)
+        for (int p = 0; p < 2; ++p) cudaFree(c->sub_buf[p][s]);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -414,6 +654,7 @@ lb_status lb_init(lb_ctx *c, const void *rho, const void *u)
 lb_status lb_set_force_field(lb_ctx *c, const void *force)
 {
     if (!c) return fail(LB_EINVAL, "lb_set_force_field: null context");
+    if (force && c->nsub > 1) return fail(LB_EINVAL, "lb_set_force_field: not available with subdomains > 1");
     const size_t nb = 3 * (size_t)c->g.N * c->rbytes;
     if (!force) {
         LB_CUDA(cudaStreamSynchronize(c->stream));
@@ -430,6 +671,12 @@ lb_status lb_step(lb_ctx *c, int n)
 {
     if (!c) return fail(LB_EINVAL, "lb_step: null context");
     if (n < 0) return fail(LB_EINVAL, "lb_step: n must be >= 0");
+    if (n == 0) return LB_OK;
+    if (c->nsub > 1) {
+        lb_status st = ensure_slabs(c);
+        if (st) return st;
+        LB_CUDA(slab_transfer(c, c->cur, true));
+    }
     bool plain_done = false;   // one step with these arguments ran outside a capture
     for (int i = 0; i < n;) {
         const LaunchArgs a = launch_args(c);
@@ -442,15 +689,14 @@ lb_status lb_step(lb_ctx *c, int n)
                 continue;
             }
         }
-        const void *src = c->buf[c->cur];
-        void *dst = c->buf[c->cur ^ 1];
-        LB_CUDA(dispatch(c->cfg.storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); }));
+        LB_CUDA(one_step(c, a, c->cur));
         c->cur ^= 1;
         ++c->t;
         plain_done = !c->fresh;
         c->fresh = false;
         ++i;
     }
+    if (c->nsub > 1) LB_CUDA(slab_transfer(c, c->cur, false));
     return LB_OK;
 }
 

@@ -39,6 +39,10 @@ struct LaunchArgs {
 // z-planes per thread of the two-node kernel (software pipelining depth).
 constexpr int kPairPlanes = LBC_PAIR_PLANES;
 
+// Launch shape of the one-node kernels: every plane of the lattice, or for a step
+// launch the planes kz0, kz0 + kzs, ... below kz1.
+inline int step_planes(const Geom &g) { return (g.kz1 - g.kz0 + g.kzs - 1) / g.kzs; }
+
 inline void launch_shape(const Geom &g, dim3 &grid, dim3 &block)
 {
     int bx = kBlockX;
@@ -103,30 +107,32 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
     S *d = static_cast<S *>(dst);
     const T *ff = static_cast<const T *>(a.force_field);
     T *rf = static_cast<T *>(a.rho_field);
+    if (use_bulk(a)) return step_bulk(a, src, dst);
+    if (use_pair(a)) return step_pair(a, src, dst);   // (with its own density pre-pass in FULL mode)
     if (a.corr == LB_CORR_FULL) {
         k_density<ST><<<grid, block, 0, a.stream>>>(s, a.g, P, D, (T)a.lid_u, rf);
     }
-    if (use_bulk(a)) return step_bulk(a, src, dst);
-    if (use_pair(a)) return step_pair(a, src, dst);
+    dim3 sgrid = grid;               // the planes this launch updates
+    sgrid.z = step_planes(a.g);
     switch (a.corr) {
     case LB_CORR_NONE:
-        k_step<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
+        k_step<ST, LB_CORR_NONE><<<sgrid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
                                                                 ff, rf, (T)a.lid_u, a.sr_key);
         break;
     case LB_CORR_LOWMACH:
-        k_step<ST, LB_CORR_LOWMACH><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1],
+        k_step<ST, LB_CORR_LOWMACH><<<sgrid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1],
                                                                    (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
         break;
     case LB_CORR_LOCAL:
         if (a.model == 1)
-            k_step<ST, LB_CORR_LOCAL | kRawModel><<<grid, block, 0, a.stream>>>(
+            k_step<ST, LB_CORR_LOCAL | kRawModel><<<sgrid, block, 0, a.stream>>>(
                 s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
         else
-            k_step<ST, LB_CORR_LOCAL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1],
+            k_step<ST, LB_CORR_LOCAL><<<sgrid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1],
                                                                      (T)a.F[2], ff, rf, (T)a.lid_u, a.sr_key);
         break;
     default:
-        k_step<ST, LB_CORR_FULL><<<grid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
+        k_step<ST, LB_CORR_FULL><<<sgrid, block, 0, a.stream>>>(s, d, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2],
                                                                 ff, rf, (T)a.lid_u, a.sr_key);
         break;
     }
@@ -134,14 +140,15 @@ cudaError_t Ops<ST>::step(const LaunchArgs &a, const void *src, void *dst)
 }
 
 // The two-node kernel covers the FP32-arithmetic storage forms on lattices with an
-// even nx, no walls normal to x, no moving lid, no FULL corrections and 32-bit
-// offsets; everything else takes the one-node kernel.
+// even nx, no walls normal to x, no moving lid and 32-bit offsets (FULL corrections
+// with round-to-nearest storage only); everything else takes the one-node kernel.
 template <int ST>
 bool Ops<ST>::use_pair(const LaunchArgs &a)
 {
     if (ST == LB_F64 || a.kernel == 1) return false;   // (kernel 3 falls back here where staging does not apply)
     if (a.model == 1 && a.sr_key != 0) return false;   // raw model with stochastic rounding: one node per thread
-    return (a.g.nx % 2 == 0) && !a.g.wall[0] && a.lid_u == 0.0 && a.corr != LB_CORR_FULL &&
+    if (a.corr == LB_CORR_FULL && a.sr_key != 0) return false;  // FULL with stochastic rounding: one node per thread
+    return (a.g.nx % 2 == 0) && !a.g.wall[0] && a.lid_u == 0.0 &&
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
 
@@ -157,7 +164,8 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
         int bx = kBlockX;
         while (bx > 1 && bx / 2 >= np) bx /= 2;
         const int by = kBlockThreads / bx;
-        const dim3 block(bx, by, 1), grid((np + bx - 1) / bx, (a.g.ny + by - 1) / by, (a.g.nz + ZC - 1) / ZC);
+        if (ZC > 1 && a.g.kzs != 1) return cudaErrorInvalidValue;   // strided planes: one plane per thread
+        const dim3 block(bx, by, 1), grid((np + bx - 1) / bx, (a.g.ny + by - 1) / by, (step_planes(a.g) + ZC - 1) / ZC);
         const Phys<float> P = phys(a);
         const DirConst<float> D = dirs(a);
         DirPtrs<S> ptr;
@@ -166,40 +174,56 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
             ptr.dst[q] = static_cast<S *>(dst) + (size_t)q * (size_t)a.g.N;
         }
         const float *ff = static_cast<const float *>(a.force_field);
+        float *rf = static_cast<float *>(a.rho_field);
         const float F0 = (float)a.F[0], F1 = (float)a.F[1], F2 = (float)a.F[2];
         const bool sr = a.sr_key != 0 && sizeof(S) == 2;
+        const bool yzw = a.g.wall[1] || a.g.wall[2];
+        if (a.corr == LB_CORR_FULL) {
+            // density pre-pass (one plane per thread), then the step with the gradients
+            const dim3 dgrid(grid.x, grid.y, step_planes(a.g));
+            if (yzw) {
+                k_density_pair<ST, true><<<dgrid, block, 0, a.stream>>>(ptr, a.g, D, rf);
+                k_step_pair<ST, LB_CORR_FULL, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
+                                                                                             ff, rf, 0u);
+            } else {
+                k_density_pair<ST, false><<<dgrid, block, 0, a.stream>>>(ptr, a.g, D, rf);
+                k_step_pair<ST, LB_CORR_FULL, ZC, false, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
+                                                                                              F2, ff, rf, 0u);
+            }
+            return cudaGetLastError();
+        }
         switch (a.corr) {
         case LB_CORR_NONE:
             if (sr)
-                k_step_pair<ST, LB_CORR_NONE, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_NONE, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff, rf,
                                                                                       a.sr_key);
             else
-                k_step_pair<ST, LB_CORR_NONE, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_NONE, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff, rf,
                                                                                        0u);
             break;
         case LB_CORR_LOWMACH:
             if (sr)
                 k_step_pair<ST, LB_CORR_LOWMACH, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
-                                                                                         ff, a.sr_key);
+                                                                                         ff, rf, a.sr_key);
             else
                 k_step_pair<ST, LB_CORR_LOWMACH, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2,
-                                                                                          ff, 0u);
+                                                                                          ff, rf, 0u);
             break;
         default:
             if (a.model == 1)
                 k_step_pair<ST, LB_CORR_LOCAL | kRawModel, ZC, false, true><<<grid, block, 0, a.stream>>>(
-                    ptr, a.g, P, D, F0, F1, F2, ff, 0u);
+                    ptr, a.g, P, D, F0, F1, F2, ff, rf, 0u);
             else if (!a.g.wall[1] && !a.g.wall[2] && sr)     // periodic in y and z: no bounce-back tests
                 k_step_pair<ST, LB_CORR_LOCAL, ZC, true, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
-                                                                                              F2, ff, a.sr_key);
+                                                                                              F2, ff, rf, a.sr_key);
             else if (!a.g.wall[1] && !a.g.wall[2])
                 k_step_pair<ST, LB_CORR_LOCAL, ZC, false, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
-                                                                                               F2, ff, 0u);
+                                                                                               F2, ff, rf, 0u);
             else if (sr)
-                k_step_pair<ST, LB_CORR_LOCAL, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff, rf,
                                                                                        a.sr_key);
             else
-                k_step_pair<ST, LB_CORR_LOCAL, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff,
+                k_step_pair<ST, LB_CORR_LOCAL, ZC, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1, F2, ff, rf,
                                                                                         0u);
             break;
         }
@@ -256,6 +280,12 @@ cudaError_t launch_bulk(const LaunchArgs &a, const void *src, void *dst)
 
 // Stage depth and CTAs per multiprocessor: two CTAs of 256 threads per SM
 // (<= 128 registers per thread) whenever two sets of stages fit in shared memory.
+#ifndef LBC_BULK16_STAGES
+#define LBC_BULK16_STAGES 4      // 2-byte storage, rows of up to 512 nodes
+#endif
+#ifndef LBC_BULK16_MINBLOCKS
+#define LBC_BULK16_MINBLOCKS 2
+#endif
 template <int ST>
 cudaError_t Ops<ST>::step_bulk(const LaunchArgs &a, const void *src, void *dst)
 {
@@ -265,7 +295,7 @@ cudaError_t Ops<ST>::step_bulk(const LaunchArgs &a, const void *src, void *dst)
         if (a.g.nx <= 512) return launch_bulk<ST, 512, 2, 2>(a, src, dst);
         return launch_bulk<ST, 1024, 2, 1>(a, src, dst);
     } else {
-        if (a.g.nx <= 512) return launch_bulk<ST, 512, 4, 2>(a, src, dst);
+        if (a.g.nx <= 512) return launch_bulk<ST, 512, LBC_BULK16_STAGES, LBC_BULK16_MINBLOCKS>(a, src, dst);
         return launch_bulk<ST, 1024, 2, 2>(a, src, dst);
     }
 }
@@ -404,12 +434,13 @@ const char *Ops<ST>::step_kernel_name(const LaunchArgs &a)
     if (use_bulk(a)) {
         const bool wide = sizeof(S) == 4, small = a.g.nx <= 512;
         const int nxmax = small ? 512 : 1024;
-        const int ns = wide ? 2 : (small ? 4 : 2);
-        const int minb = (wide && !small) ? 1 : 2;
+        const int ns = wide ? 2 : (small ? LBC_BULK16_STAGES : 2);
+        const int minb = (wide && !small) ? 1 : (!wide && small ? LBC_BULK16_MINBLOCKS : 2);
         snprintf(buf, sizeof(buf), "k_step_bulk<%s,%s,%d,%d,%d>", storage_name(ST), corr_name(a.corr), nxmax, ns,
                  minb);
     } else if (use_pair(a)) {
-        const bool yzw = a.g.wall[1] || a.g.wall[2] || a.model == 1 || a.corr != LB_CORR_LOCAL;
+        const bool yzw = a.g.wall[1] || a.g.wall[2] || a.model == 1 ||
+                         (a.corr != LB_CORR_LOCAL && a.corr != LB_CORR_FULL);
         snprintf(buf, sizeof(buf), "k_step_pair<%s,%s%s,%d,%s,%s>", storage_name(ST), corr_name(a.corr),
                  a.model == 1 ? "|RAW" : "", kPairPlanes,
                  (a.sr_key != 0 && sizeof(S) == 2) ? "true" : "false", yzw ? "walls" : "periodic");

@@ -41,11 +41,13 @@ class Lattice:
     rounding: "nearest" or "stochastic" (FP16/BF16 storage only).
     model: "central" (3DCCM) or "raw" (3DCRM: raw moments relaxed with the same corrected
     equilibria; LOCAL corrections only).
+    subdomains: P > 1 steps the lattice as P z-slabs exchanging one-plane halos through
+    device memory (bit-identical to one domain; z periodic, no FULL, no force field).
     """
 
     def __init__(self, nx, ny, nz, r_y=1.0, r_z=1.0, nu=0.01, zeta=0.0, cs2=0.0, storage="f32",
                  corr="local", walls="", force=(0.0, 0.0, 0.0), lid_u=0.0, stream=None, device=None,
-                 kernel="auto", rounding="nearest", rounding_seed=0, model="central"):
+                 kernel="auto", rounding="nearest", rounding_seed=0, model="central", subdomains=1):
         self.lib = load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
@@ -63,6 +65,7 @@ class Lattice:
         cfg.rounding = {"nearest": 0, "stochastic": 1}[rounding]
         cfg.rounding_seed = rounding_seed
         cfg.model = {"central": 0, "raw": 1}[model]
+        cfg.subdomains = int(subdomains)
         self.cfg = cfg
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
