@@ -50,10 +50,12 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
 
 def variant_options(var: str) -> dict:
     """A bench variant is a storage form with optional suffixes: "+sr" stochastic
-    rounding of 16-bit stores, "+full" the FULL corrections (density-gradient terms)."""
+    rounding of 16-bit stores, "+full" the FULL corrections (density-gradient terms),
+    "+pN" the lattice updated as N z-slabs exchanging one-plane halos (same results)."""
     parts = var.split("+")
+    sub = [int(p[1:]) for p in parts[1:] if p.startswith("p") and p[1:].isdigit()]
     return {"storage": parts[0], "rounding": "stochastic" if "sr" in parts[1:] else "nearest",
-            "corr": "full" if "full" in parts[1:] else None}
+            "corr": "full" if "full" in parts[1:] else None, "subdomains": sub[0] if sub else 1}
 
 
 def bytes_per_node(var: str) -> int:
@@ -69,7 +71,7 @@ def bytes_per_node(var: str) -> int:
 # capture of the named kernel on the 512x128x128 decaying-flow case, scaled by the node
 # count; only reported for the kernel those counters were taken on.
 TRAFFIC_PER_NODE = {("decaying", "k_step_pair<F32,LOCAL,1,false>"): (906.041088e6 + 866.070528e6) / 8388608}
-VARIANTS = ["f32", "f32s", "bf16s", "f16s", "bf16s+sr", "f16s+sr", "f32+full"]
+VARIANTS = ["f32", "f32s", "bf16s", "f16s", "bf16s+sr", "f16s+sr", "f32+full", "f32+p4"]
 
 
 def measured_peaks():
@@ -195,7 +197,7 @@ def run_ours(args, rank, world):
         vo = variant_options(var)
         lat = Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=vo["storage"],
                       corr=vo["corr"] or w["corr"], stream=stream, device=dev, kernel=args.kernel, walls=w["walls"],
-                      force=w["force"], rounding=vo["rounding"])
+                      force=w["force"], rounding=vo["rounding"], subdomains=vo["subdomains"])
         with torch.cuda.stream(stream):
             lat.init(rho_t, u_t)
             lat.step(args.warmup)
@@ -265,8 +267,11 @@ def run_ours(args, rank, world):
     control = errors(trajectory("f64", u_t.double() + 1e-6 * up, "auto", ccp), ref)
     del up
     for var in variants:
-        if variant_options(var)["corr"] is not None:
-            results[var]["u_rel_err_vs_f64"] = None     # another scheme than the FP64 reference's
+        vo = variant_options(var)
+        if vo["corr"] is not None or vo["subdomains"] > 1:
+            # another scheme than the FP64 reference's; or the same state as the undecomposed
+            # variant bit for bit (the slab decomposition changes no arithmetic)
+            results[var]["u_rel_err_vs_f64"] = None
             continue
         results[var]["u_rel_err_vs_f64"] = errors(trajectory(var, u_t, args.kernel), ref)
     results["_control_f64_perturbed_1e-6"] = control
@@ -388,7 +393,7 @@ def run_study(args):
                     emit({"study": "stability", "grid": [nx, ny, nz], "r": r, "s": s, "model": model,
                           "omega_nu": wn, "omega_xi": 1.0, "U_max": U, "steps": args.study_steps})
     elif args.study == "xi":               # Fig. 9: U_max vs omega_nu for omega_xi = 0.5, 1.0, 1.4
-        for corr in ("local", "none"):
+        for corr in args.study_corr.split(","):
             for wb in (0.5, 1.0, 1.4):
                 for wn in omegas:
                     U = studies.max_stable_lid_velocity(30, 60, 30, 0.5, 1.0, 0.08, wn, wb, "central",
@@ -401,6 +406,54 @@ def run_study(args):
                 re = studies.max_stable_reynolds(nx, ny, nz, 0.5, 1.0, 0.08, 0.2, model, args.study_steps)
                 emit({"study": "reynolds", "grid": [nx, ny, nz], "r": 0.5, "s": 1.0, "model": model, "U": 0.2,
                       "Re_max": re, "steps": args.study_steps})
+    elif args.study == "channel":          # channel 768x192x384 long run, reduced-precision storage vs FP32
+        import torch
+        from paper_2107_14774_gb300 import Lattice
+        w = WORKLOADS["channel"]
+        n = (w["nx"], w["ny"], w["nz"])
+        rho, u, fx = synth.channel(*n, w["r_y"], w["r_z"], 0.02, w["nu"], 0.05, seed=5)
+        h = n[1] * w["r_y"]
+        yw = (np.arange(n[1]) + 0.5) * w["r_y"]
+        laminar = torch.from_numpy(4 * 0.02 * yw * (h - yw) / h ** 2)
+        cps = sorted({int(v) for v in args.study_checkpoints.split(",")})
+        rho_t = torch.from_numpy(rho.astype(np.float32)).cuda()
+        u_t = torch.from_numpy(u.astype(np.float32)).cuda()
+        del rho, u
+        stream = torch.cuda.Stream()
+        ref = {}
+        for var in ["f32"] + [v for v in args.study_variants.split(",") if v != "f32"]:
+            vo = variant_options(var)
+            lat = Lattice(*n, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage=vo["storage"],
+                          corr=w["corr"], stream=stream, walls=w["walls"], force=(fx, 0.0, 0.0),
+                          rounding=vo["rounding"])
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                lat.init(rho_t, u_t)
+            m0 = lat.reduce()
+            done, t0 = 0, time.time()
+            for cp in cps:
+                lat.step(cp - done)
+                done = cp
+                m = lat.reduce()
+                ut = lat.moments()[1][0].double()             # u_x [nz, ny, nx]
+                prof = ut.mean(dim=(0, 2)).cpu()              # mean over x and z: u_x(y)
+                rec = {"study": "channel", "variant": var, "kernel": lat.step_kernel, "step": cp,
+                       "mass_drift_rel": float(m[0] / m0[0] - 1.0),
+                       "profile_vs_laminar_rel_l2": float(torch.linalg.vector_norm(prof - laminar)
+                                                          / torch.linalg.vector_norm(laminar)),
+                       "profile_centre": float(prof[n[1] // 2]), "laminar_centre": float(laminar[n[1] // 2]),
+                       "fluctuation_rms": float((ut - prof.to(ut.device)[None, :, None]).pow(2).mean().sqrt()),
+                       "seconds": round(time.time() - t0, 1)}
+                if var == "f32":
+                    ref[cp] = lat.moments()[1].double().cpu()
+                else:
+                    uu = lat.moments()[1].double().cpu()
+                    rec["u_rel_l2_vs_f32"] = float(torch.linalg.vector_norm(uu - ref[cp]) /
+                                                   torch.linalg.vector_norm(ref[cp]))
+                    del uu
+                emit(rec)
+            lat.close()
+            torch.cuda.empty_cache()
     elif args.study == "adjoint":          # discrete adjoint, 128x64x64, T = 500, K = 50, FP32
         import torch
         import synth
@@ -467,10 +520,17 @@ def main():
                     help="kernel selection passed to the library (auto = two nodes per thread where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")
-    ap.add_argument("--study", default=None, choices=["stability", "xi", "reynolds", "cavity", "adjoint"],
+    ap.add_argument("--study", default=None, choices=["stability", "xi", "reynolds", "cavity", "adjoint", "channel"],
                     help="run a parameter study of the paper instead of the benchmark (one JSON line per point): "
                          "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6, "
-                         "adjoint = timing of the checkpointed adjoint on the 128x64x64 case")
+                         "adjoint = timing of the checkpointed adjoint on the 128x64x64 case, "
+                         "channel = 768x192x384 channel run of reduced-precision storage against FP32")
+    ap.add_argument("--study-corr", default="full,local,none",
+                    help="correction modes of the omega_xi study (Fig. 9)")
+    ap.add_argument("--study-checkpoints", default="1000,10000,50000",
+                    help="step counts at which the channel study reports (the last is the run length)")
+    ap.add_argument("--study-variants", default="f32,bf16s,bf16s+sr,f16s+sr",
+                    help="storage forms of the channel study (f32 is the reference run)")
     ap.add_argument("--study-steps", type=int, default=100_000, help="steps a stable run must survive")
     ap.add_argument("--omegas", default="1.5,1.6,1.7,1.8,1.9,1.95,1.98",
                     help="omega_nu values of the stability studies")
