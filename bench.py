@@ -70,7 +70,7 @@ def bytes_per_node(var: str) -> int:
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu
 # capture of the named kernel on the 512x128x128 decaying-flow case, scaled by the node
 # count; only reported for the kernel those counters were taken on.
-TRAFFIC_PER_NODE = {("decaying", "k_step_pair<F32,LOCAL,1,false>"): (906.041088e6 + 866.070528e6) / 8388608}
+TRAFFIC_PER_NODE = {("decaying", "k_step_pair<F32,LOCAL,1,false,periodic>"): (906.026496e6 + 855.318784e6) / 8388608}
 VARIANTS = ["f32", "f32s", "bf16s", "f16s", "bf16s+sr", "f16s+sr", "f32+full", "f32+p4"]
 
 
