@@ -456,7 +456,6 @@ def run_study(args):
             torch.cuda.empty_cache()
     elif args.study == "adjoint":          # discrete adjoint, 128x64x64, T = 500, K = 50, FP32
         import torch
-        import synth
         from paper_2107_14774_gb300 import Lattice
         n, T, K = (128, 64, 64), 500, 50
         rho, u = synth.solenoidal_random(*n, 1.0, 0.5, 4.0, 0.01, seed=4)
