@@ -295,13 +295,15 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
     # end to end through the public API with pinned host buffers: every step copies its
     # inputs (rho, u) host->device (lb_init), runs one fused step and reads the resulting
     # fields device->host (lb_moments).  Measured two ways: one context doing that
-    # serially, and two contexts on their own streams taking alternate steps, so that one
-    # step's upload overlaps the previous step's download and compute (independent inputs
-    # streamed through the library, each step with its own copies in both directions).
+    # serially, and D contexts on their own streams taking the steps in turn, so that the
+    # upload of one step overlaps the download and compute of the steps before it
+    # (independent inputs streamed through the library, each step with its own copies in
+    # both directions).
+    D = max(1, args.e2e_contexts)
     rho_h = torch.from_numpy(rho.astype(np.float32)).pin_memory()
     u_h = torch.from_numpy(u.astype(np.float32)).pin_memory()
-    outs = [(torch.empty_like(rho_h).pin_memory(), torch.empty_like(u_h).pin_memory()) for _ in range(2)]
-    streams = [stream, torch.cuda.Stream(dev)]
+    outs = [(torch.empty_like(rho_h).pin_memory(), torch.empty_like(u_h).pin_memory()) for _ in range(D)]
+    streams = [stream] + [torch.cuda.Stream(dev) for _ in range(D - 1)]
     lats = [Lattice(*dims, r_y=w["r_y"], r_z=w["r_z"], nu=w["nu"], cs2=w["cs2"], storage="f32", corr=w["corr"],
                     stream=s, device=dev, kernel=args.kernel, walls=w["walls"], force=w["force"]) for s in streams]
     e2e_steps = max(4, min(args.steps, 20))
@@ -311,14 +313,29 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
             lats[0].init(rho_h, u_h).step(1).moments(*outs[0])
 
     def pipelined(n):
-        for i in range(n + 1):
+        for i in range(n + D - 1):
             if i < n:
-                lats[i % 2].init(rho_h, u_h).step(1)          # asynchronous: upload, step
-            if i >= 1:
-                lats[(i - 1) % 2].moments(*outs[(i - 1) % 2])  # download of the previous step, waits for it
+                lats[i % D].init(rho_h, u_h).step(1)          # asynchronous: upload, step
+            j = i - (D - 1)
+            if j >= 0:
+                lats[j % D].moments(*outs[j % D])              # download of step j, waits for it
+
+    # the host link alone: one step's bytes up and down at once, no compute
+    up = (torch.empty(rho_h.shape, dtype=rho_h.dtype, device=dev), torch.empty(u_h.shape, dtype=u_h.dtype, device=dev))
+    down = (torch.zeros_like(up[0]), torch.zeros_like(up[1]))
+
+    def link(n):
+        for _ in range(n):
+            with torch.cuda.stream(streams[0]):
+                up[0].copy_(rho_h, non_blocking=True)
+                up[1].copy_(u_h, non_blocking=True)
+            with torch.cuda.stream(streams[-1] if D > 1 else torch.cuda.Stream(dev)):
+                outs[0][0].copy_(down[0], non_blocking=True)
+                outs[0][1].copy_(down[1], non_blocking=True)
+            torch.cuda.synchronize(dev)
 
     timings = {}
-    for name, fn in (("serial", serial), ("pipelined", pipelined)):
+    for name, fn in (("serial", serial), ("pipelined", pipelined), ("link", link)):
         fn(2)
         barrier()
         torch.cuda.synchronize(dev)
@@ -328,13 +345,18 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
         timings[name] = allreduce_max(time.perf_counter() - t0, dev)
     for lat in lats:
         lat.close()
+    del up, down
     e2e = {"value": aggregate_mlups(N, e2e_steps, world, timings["pipelined"]), "unit": "MLUPS",
-           "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N,
-           "what": "per step: lb_init from pinned host rho,u + lb_step(1) + lb_moments to pinned host; two "
-                   "contexts on their own streams take alternate steps (upload of one overlaps the other's "
-                   "download)",
+           "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N, "contexts": D,
+           "what": f"per step: lb_init from pinned host rho,u + lb_step(1) + lb_moments to pinned host; {D} "
+                   "contexts on their own streams take the steps in turn (the upload of one step overlaps the "
+                   "download and compute of the steps before it)",
            "serial": {"value": aggregate_mlups(N, e2e_steps, world, timings["serial"]), "unit": "MLUPS",
-                      "what": "the same with one context, each step's copies and step in sequence"}}
+                      "what": "the same with one context, each step's copies and step in sequence"},
+           "link_bound": {"value": aggregate_mlups(N, e2e_steps, world, timings["link"]), "unit": "MLUPS",
+                          "what": "the same bytes copied between pinned host and device memory, both directions "
+                                  "at once, without the library"}}
+    e2e["link_frac"] = e2e["value"] / e2e["link_bound"]["value"]
     return e2e
 
 
@@ -418,9 +440,10 @@ def run_study(args):
             for wb in (0.5, 1.0, 1.4):
                 for wn in omegas:
                     U = studies.max_stable_lid_velocity(30, 60, 30, 0.5, 1.0, 0.08, wn, wb, "central",
-                                                        args.study_steps, corr=corr)
+                                                        args.study_steps, corr=corr, ramp_steps=args.study_ramp)
                     emit({"study": "xi", "grid": [30, 60, 30], "r": 0.5, "s": 1.0, "model": "central",
-                          "corr": corr, "omega_nu": wn, "omega_xi": wb, "U_max": U, "steps": args.study_steps})
+                          "corr": corr, "omega_nu": wn, "omega_xi": wb, "U_max": U, "steps": args.study_steps,
+                          "lid_ramp_steps": args.study_ramp})
     elif args.study == "reynolds":         # Fig. 10: Re_max at U = 0.2, r = 0.5, s = 1, cs2 = 0.08
         for (nx, ny, nz) in [(40, 80, 40), (50, 100, 50), (90, 180, 90)]:
             for model in ("central", "raw"):
@@ -536,7 +559,7 @@ def main():
                          "bf16s+sr / f16s+sr: stochastic rounding)")
     ap.add_argument("--workload", default="decaying", choices=sorted(WORKLOADS),
                     help="decaying: 512x256x256 periodic (default); channel: 768x192x384 with y walls")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged", "march"],
                     help="kernel selection passed to the library (auto = two nodes per thread where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")
@@ -545,8 +568,12 @@ def main():
                          "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6, "
                          "adjoint = timing of the checkpointed adjoint on the 128x64x64 case, "
                          "channel = 768x192x384 channel run of reduced-precision storage against FP32")
+    ap.add_argument("--e2e-contexts", type=int, default=3,
+                    help="contexts taking the end-to-end steps in turn (1: no overlap)")
     ap.add_argument("--study-corr", default="full,local,none",
                     help="correction modes of the omega_xi study (Fig. 9)")
+    ap.add_argument("--study-ramp", type=int, default=0,
+                    help="xi study: bring the lid up to speed linearly over this many steps (0: impulsive start)")
     ap.add_argument("--study-checkpoints", default="1000,10000,50000",
                     help="step counts at which the channel study reports (the last is the run length)")
     ap.add_argument("--study-variants", default="f32,bf16s,bf16s+sr,f16s+sr",

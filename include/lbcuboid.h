@@ -103,7 +103,10 @@ typedef struct {
     int kernel;            /* 0: automatic (two nodes per thread where the lattice allows it,
                               else one node per thread); 1: one node per thread; 2: two nodes
                               per thread; 3: row-staged through shared memory with bulk copies
-                              (4- and 2-byte storage, rows of up to 1024 nodes) */
+                              (4- and 2-byte storage, rows of up to 1024 nodes); 4: two nodes per
+                              thread marching along z, the next plane's sources copied into
+                              shared memory while the current plane is collided (16-bit storage,
+                              LOCAL corrections, rows of at least 64 nodes; else as 0) */
     int model;             /* collision model: 0 = central moments (3DCCM, Sec. 3.2), 1 = raw
                               moments with the same corrected equilibria (3DCRM, Sec. 3.1 raw
                               formulation and Sec. 7); model 1 needs LB_CORR_LOCAL and is not
@@ -197,6 +200,15 @@ lb_status lb_set_force(lb_ctx *ctx, const double force[3]);
  * directly (App. D; they map to nu and xi through Eq. 53) for the steps enqueued
  * after this call.  LB_EINVAL unless 0 < omega < 2 for both. */
 lb_status lb_set_rates(lb_ctx *ctx, double omega_nu, double omega_xi);
+
+/* Replace the lid velocity (the x velocity of the wall at j = ny - 1/2 in the
+ * momentum-augmented bounce-back of Sec. 4, Eq. 69) for the steps enqueued after this
+ * call: the step from t to t + 1 (collision at t, then streaming with the wall term into
+ * t + 1) uses the velocity set before the lb_step call that runs it, as lb_set_force
+ * does for the force.  A lid started from rest and brought up to speed over many steps
+ * is set this way between lb_step calls.  LB_EINVAL on a non-finite value, or on a
+ * non-zero one without walls normal to y. */
+lb_status lb_set_lid(lb_ctx *ctx, double lid_u);
 
 /* Mean kinetic energy J = (1/N) sum_x rho |u|^2 / 2 of the current populations,
  * u including the F/2 shift (Eq. 12); FP64 sum, deterministic.  Synchronises. */

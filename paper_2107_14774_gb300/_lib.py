@@ -65,6 +65,7 @@ SIGNATURES = {
     "lb_time_step": (ctypes.c_longlong, [_CTX]),
     "lb_set_force": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double)]),
     "lb_set_rates": (ctypes.c_int, [_CTX, ctypes.c_double, ctypes.c_double]),
+    "lb_set_lid": (ctypes.c_int, [_CTX, ctypes.c_double]),
     "lb_objective_ke": (ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double)]),
     "lb_adjoint_ke": (ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]),

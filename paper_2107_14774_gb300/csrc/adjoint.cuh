@@ -436,10 +436,11 @@ k_adjoint_seed(const typename Codec<ST>::S *__restrict__ src, Geom g, Phys<typen
 // One step of the discrete adjoint (see the top of this file).  src = stored state
 // S^n (pull layout, so that pulling gives f^n); lam_in = lambda^{n+1} and lam_out =
 // lambda^n in natural layout [27][N].
-// Resident CTAs per SM requested from the compiler.  Left free the adjoint step takes 168
-// registers (3 CTAs of 128 threads per SM); at four CTAs (128 registers, 44 B spilled) the
-// whole lb_adjoint_ke call on 128x64x64, T = 500 ran 21 % faster on GB300 (56.8 vs 72.0 ms;
-// three CTAs 60.2 ms, five CTAs 62.8 ms with 624 B spilled).
+// Resident CTAs per SM requested from the compiler.  Left free, the adjoint step with LOCAL
+// corrections takes 188 registers (two CTAs of 128 threads per SM).  At four CTAs (128
+// registers, 44 B spilled) the whole lb_adjoint_ke call on 128x64x64 with a per-node force
+// field, T = 500, K = 50, took 56.8 ms on GB300 against 72.0 ms left free (three CTAs
+// 60.2 ms, five CTAs 62.8 ms with 624 B spilled).
 #ifndef LBC_ADJ_MINBLOCKS
 #define LBC_ADJ_MINBLOCKS 4
 #endif

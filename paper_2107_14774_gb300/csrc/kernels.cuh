@@ -514,6 +514,144 @@ k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
     }
 }
 
+// Two nodes per thread marching along z, with the sources of the next plane staged in
+// shared memory (16-bit storage).  A warp owns one 64-node segment of row j (32 words,
+// a word being the two 16-bit values of a node pair) and kMarchPlanes consecutive
+// planes.  For each direction it copies the 32 words of the segment in the source row,
+// plus the word left of the segment (e_x = +1) or right of it (e_x = -1), into shared
+// memory with per-lane 4-byte cp.async, and cuts the x-shifted pairs out of two
+// neighbouring words there.  The copies of plane k + 1 are issued as soon as plane k
+// has been read out of the stage, so they are in flight while plane k is collided and
+// stored, without holding registers.
+#ifndef LBC_MARCH_PLANES
+#define LBC_MARCH_PLANES 8
+#endif
+#ifndef LBC_MARCH_MINBLOCKS
+#define LBC_MARCH_MINBLOCKS 5
+#endif
+constexpr int kMarchPlanes = LBC_MARCH_PLANES;
+constexpr int kStageWords = kBlockX + 2;   // the segment's words and one on either side
+
+__device__ __forceinline__ void cp_async4(unsigned *smem, const unsigned *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issue the copies of plane k into stage[a][0 .. kStageWords): the lane's own word
+// (index wi of its row) at 1 + lane; lane 0 adds the word wl left of the segment, the
+// last active lane the word wr right of it.  Across a y or z wall the source is the
+// node's own word of the opposite direction (half-way bounce-back).
+template <int ST, bool YZW>
+__device__ __forceinline__ void march_issue(unsigned (*stage)[kStageWords], const DirPtrs<typename Codec<ST>::S> &ptr,
+                                            const Geom &g, int lane, bool left, bool right, unsigned wi, unsigned wl,
+                                            unsigned wr, const int (&ys)[3], const bool (&yo)[3], int k)
+{
+    int zs[3];
+    bool zo[3];
+    axis_sources(k, g.nz, g.wall[2], zs, zo);
+    const unsigned hx = (unsigned)g.nx >> 1, hxy = hx * (unsigned)g.ny;   // words per row, per plane
+    unsigned rowbase[3][3];
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) rowbase[cy][cz] = (unsigned)zs[cz] * hxy + (unsigned)ys[cy] * hx;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
+        if (YZW && (yo[cy] | zo[cz])) {
+            cp_async4(&stage[a][1 + lane], reinterpret_cast<const unsigned *>(ptr.src[opp(a)]) + rowbase[1][1] + wi);
+        } else {
+            const unsigned *p = reinterpret_cast<const unsigned *>(ptr.src[a]) + rowbase[cy][cz];
+            cp_async4(&stage[a][1 + lane], p + wi);
+            if (cx == 2 && left) cp_async4(&stage[a][0], p + wl);
+            if (cx == 0 && right) cp_async4(&stage[a][2 + lane], p + wr);
+        }
+    }
+    cp_async_commit();
+}
+
+// The raw words of the lane's two nodes at plane k from the stage (the element of the
+// first node in the low half, as the loads of pair_fetch give them).
+template <int ST, bool YZW>
+__device__ __forceinline__ void march_read(unsigned (&raw)[Q], const unsigned (*stage)[kStageWords], const Geom &g,
+                                           int lane, const bool (&yo)[3], int k)
+{
+    int zs[3];
+    bool zo[3];
+    axis_sources(k, g.nz, g.wall[2], zs, zo);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
+        if (cx == 1 || (YZW && (yo[cy] | zo[cz])))
+            raw[a] = stage[a][1 + lane];
+        else if (cx == 2)   // ex = +1: sources i0 - 1 (high half of the left word), i0
+            raw[a] = __byte_perm(stage[a][lane], stage[a][1 + lane], 0x5432);
+        else                // ex = -1: sources i0 + 1, i0 + 2 (low half of the right word)
+            raw[a] = __byte_perm(stage[a][1 + lane], stage[a][2 + lane], 0x5432);
+    }
+}
+
+template <int ST, int CORR, bool SR, bool YZW>
+__global__ void __launch_bounds__(kBlockThreads, LBC_MARCH_MINBLOCKS)
+k_step_march(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
+             float F2s, const float *__restrict__ ff, unsigned sr_key)
+{
+    using IO = PairIO<ST>;
+    static_assert(sizeof(typename Codec<ST>::S) == 2, "k_step_march stages 16-bit storage");
+    __shared__ unsigned stage_all[kBlockThreads / kBlockX][Q][kStageWords];
+    const int lane = threadIdx.x;   // blockDim.x == kBlockX: one warp per row segment
+    const int i0 = 2 * ((int)blockIdx.x * kBlockX + lane);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = g.kz0 + (int)blockIdx.z * kMarchPlanes;
+    if (j >= g.ny) return;          // the whole warp
+    const bool on = i0 < g.nx;
+    const unsigned act = __ballot_sync(0xffffffffu, on);
+    if (!on) return;
+    const int last = 31 - __clz(act);   // the active lanes are 0 .. last
+    const int kend = min(k0 + kMarchPlanes, g.kz1);
+    unsigned (*stage)[kStageWords] = stage_all[threadIdx.y];
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    int ys[3];
+    bool yo[3];
+    axis_sources(j, g.ny, g.wall[1], ys, yo);
+    const unsigned wi = (unsigned)i0 >> 1;
+    const unsigned wl = (i0 == 0 ? nx : (unsigned)i0) / 2u - 1u;   // word of node i0 - 1 (periodic in x)
+    const unsigned wr = (i0 + 2 == g.nx) ? 0u : wi + 1u;            // word of node i0 + 2
+    march_issue<ST, YZW>(stage, ptr, g, lane, lane == 0, lane == last, wi, wl, wr, ys, yo, k0);
+    for (int k = k0; k < kend; ++k) {
+        cp_async_wait_all();
+        __syncwarp(act);
+        unsigned raw[Q];
+        march_read<ST, YZW>(raw, stage, g, lane, yo, k);
+        __syncwarp(act);
+        if (k + 1 < kend) march_issue<ST, YZW>(stage, ptr, g, lane, lane == 0, lane == last, wi, wl, wr, ys, yo, k + 1);
+        F2 h[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) h[a] = IO::dec(raw[a], D.w[a], D.iscale[a]);
+        const unsigned self = (unsigned)k * nxy + (unsigned)j * nx + (unsigned)i0;
+        F2 Fx(F0), Fy(F1), Fz(F2s);
+        if (ff) {
+            const unsigned N = (unsigned)g.N;
+            Fx += F2(__ldg(reinterpret_cast<const float2 *>(ff + self)));
+            Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
+            Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
+        }
+        if constexpr (SR) {
+            unsigned rs = hash32((self + (unsigned)g.zofs * nxy) * 0x9e3779b1u + sr_key) | 1u;
+            collide_pair<CORR>(
+                h, [&](int a, F2 v) { IO::st2sr(ptr.dst[a] + self, v, D.w[a], D.scale[a], xorshift32(rs)); }, P, Fx,
+                Fy, Fz);
+        } else {
+            collide_pair<CORR>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); }, P, Fx, Fy,
+                               Fz);
+        }
+    }
+}
+
 // Density of every node (pre-pass of LB_CORR_FULL).
 template <int ST>
 __global__ void __launch_bounds__(kBlockThreads)

@@ -83,6 +83,10 @@ struct lb_ctx {
     // lb_init / lb_set_populations (the moving-lid term belongs to streaming after
     // a collision, so it is not applied when those populations are read).
     bool fresh;
+    // Lid velocity of the step whose collision wrote the stored state: the next read
+    // streams that state, and the moving-wall term of that streaming belongs to the
+    // same step (so a lid changed between lb_step calls acts from the next step on).
+    double lid_state;
     int *err;               // error word of the bounded waits of the staged kernel
     int sm_count;
     // CUDA graphs of kGraphSteps consecutive steps starting from buffer 0 / 1, with
@@ -118,7 +122,7 @@ LaunchArgs launch_args(const lb_ctx *c)
     a.wn = c->wn;
     a.wb = c->wb;
     for (int i = 0; i < 3; ++i) a.F[i] = c->cfg.force[i];
-    a.lid_u = c->fresh ? 0.0 : c->cfg.lid_u;
+    a.lid_u = c->fresh ? 0.0 : c->lid_state;
     for (int q = 0; q < Q; ++q) {
         a.w[q] = c->w[q];
         a.scale[q] = c->scale[q];
@@ -499,7 +503,7 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (cfg->storage < LB_F64 || cfg->storage > LB_BF16_SHIFTED) return fail(LB_EINVAL, "lb_create_ex: bad storage");
     if (cfg->corr < LB_CORR_NONE || cfg->corr > LB_CORR_FULL) return fail(LB_EINVAL, "lb_create_ex: bad corr");
     if (cfg->wall_mask & ~7u) return fail(LB_EINVAL, "lb_create_ex: bad wall_mask");
-    if (cfg->kernel < 0 || cfg->kernel > 3) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
+    if (cfg->kernel < 0 || cfg->kernel > 4) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
     if (cfg->rounding < 0 || cfg->rounding > 1) return fail(LB_EINVAL, "lb_create_ex: bad rounding mode");
     if (cfg->rounding == 1 && cfg->storage != LB_F16_SHIFTED && cfg->storage != LB_BF16_SHIFTED)
         return fail(LB_EINVAL, "lb_create_ex: stochastic rounding applies to FP16/BF16 storage only");
@@ -531,6 +535,7 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     lb_ctx *c = new lb_ctx();
     std::memset(static_cast<void *>(c), 0, sizeof(*c));
     c->cfg = *cfg;
+    c->lid_state = cfg->lid_u;
     c->cfg.cs2 = cs2;
     c->cs2 = cs2;
     c->wn = wn;
@@ -680,7 +685,8 @@ lb_status lb_step(lb_ctx *c, int n)
     bool plain_done = false;   // one step with these arguments ran outside a capture
     for (int i = 0; i < n;) {
         const LaunchArgs a = launch_args(c);
-        if (plain_done && n - i >= kGraphSteps && !c->graph_off && c->stream != nullptr && c->cfg.rounding == 0) {
+        if (plain_done && n - i >= kGraphSteps && !c->graph_off && c->stream != nullptr && c->cfg.rounding == 0 &&
+            c->lid_state == c->cfg.lid_u) {
             cudaGraphExec_t x = graph_for(c, a);
             if (x) {
                 LB_CUDA(cudaGraphLaunch(x, c->stream));
@@ -694,6 +700,7 @@ lb_status lb_step(lb_ctx *c, int n)
         ++c->t;
         plain_done = !c->fresh;
         c->fresh = false;
+        c->lid_state = c->cfg.lid_u;
         ++i;
     }
     if (c->nsub > 1) LB_CUDA(slab_transfer(c, c->cur, false));
@@ -800,6 +807,7 @@ lb_status lb_set_state(lb_ctx *c, const void *src, long long time_step)
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->t = time_step;
     c->fresh = false;
+    c->lid_state = c->cfg.lid_u;
     return LB_OK;
 }
 
@@ -820,6 +828,16 @@ lb_status lb_set_rates(lb_ctx *c, double omega_nu, double omega_xi)
         return fail(LB_EINVAL, "lb_set_rates: relaxation rates must lie in (0, 2)");
     c->wn = omega_nu;
     c->wb = omega_xi;
+    return LB_OK;
+}
+
+lb_status lb_set_lid(lb_ctx *c, double lid_u)
+{
+    if (!c) return fail(LB_EINVAL, "lb_set_lid: null context");
+    if (!std::isfinite(lid_u)) return fail(LB_EINVAL, "lb_set_lid: non-finite velocity");
+    if (lid_u != 0.0 && !(c->cfg.wall_mask & LB_WALL_Y))
+        return fail(LB_EINVAL, "lb_set_lid: a moving lid needs walls normal to y");
+    c->cfg.lid_u = lid_u;
     return LB_OK;
 }
 
@@ -881,7 +899,8 @@ lb_status lb_adjoint_ke(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2],
     if (T < 1 || K < 1) return fail(LB_EINVAL, "lb_adjoint_ke: T and K must be >= 1");
     if (c->cfg.corr == LB_CORR_FULL) return fail(LB_EINVAL, "lb_adjoint_ke: corrections FULL are not supported");
     if (c->cfg.model != 0) return fail(LB_EINVAL, "lb_adjoint_ke: the raw-moment model is not supported");
-    if (c->cfg.lid_u != 0.0) return fail(LB_EINVAL, "lb_adjoint_ke: a moving lid is not supported");
+    if (c->cfg.lid_u != 0.0 || c->lid_state != 0.0)
+        return fail(LB_EINVAL, "lb_adjoint_ke: a moving lid is not supported");
     if (c->cfg.rounding != 0) return fail(LB_EINVAL, "lb_adjoint_ke: needs round-to-nearest storage");
     if (K > T) K = T;
     const size_t sb = lb_state_bytes(c);

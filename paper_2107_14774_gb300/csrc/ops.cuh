@@ -27,7 +27,8 @@ struct LaunchArgs {
     cudaStream_t stream;
     const void *force_field;  // device, compute type, [3][N] or null
     void *rho_field;          // device, compute type, [N] (FULL) or null
-    int kernel;               // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 row-staged
+    int kernel;               // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 row-staged,
+                              // 4 two nodes per thread marching along z with staged sources
     int *err;                 // device error word of the bounded waits (bulk kernel)
     int sm_count;             // multiprocessors of the device
     unsigned sr_key;          // non-zero: stochastic rounding of 16-bit stores with this step key
@@ -72,6 +73,7 @@ struct Ops {
 
     static cudaError_t step(const LaunchArgs &a, const void *src, void *dst);
     static bool use_pair(const LaunchArgs &a);
+    static bool use_march(const LaunchArgs &a);
     static cudaError_t step_pair(const LaunchArgs &a, const void *src, void *dst);
     static bool use_bulk(const LaunchArgs &a);
     static cudaError_t step_bulk(const LaunchArgs &a, const void *src, void *dst);
@@ -152,6 +154,16 @@ bool Ops<ST>::use_pair(const LaunchArgs &a)
            (unsigned long long)Q * (unsigned long long)a.g.N < (1ull << 32);
 }
 
+// The z-marching kernel (on request, kernel 4): 16-bit storage on a lattice the
+// two-node kernel takes, LOCAL corrections of the central-moment model, contiguous
+// planes and rows of at least 64 nodes (one warp per 64-node segment).
+template <int ST>
+bool Ops<ST>::use_march(const LaunchArgs &a)
+{
+    return sizeof(S) == 2 && a.kernel == 4 && use_pair(a) && a.corr == LB_CORR_LOCAL && a.model == 0 &&
+           a.g.kzs == 1 && a.g.nx >= 2 * kBlockX;
+}
+
 #ifndef LBC_OPS_SKIP_PAIR   // defined in the step_*_pair.cu translation units
 template <int ST>
 cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
@@ -159,6 +171,36 @@ cudaError_t Ops<ST>::step_pair(const LaunchArgs &a, const void *src, void *dst)
     if constexpr (ST == LB_F64) {
         return cudaErrorInvalidValue;
     } else {
+        if constexpr (sizeof(S) == 2) {
+            if (use_march(a)) {
+                const dim3 block(kBlockX, kBlockThreads / kBlockX, 1);
+                const dim3 grid((a.g.nx / 2 + kBlockX - 1) / kBlockX, (a.g.ny + block.y - 1) / block.y,
+                                (a.g.kz1 - a.g.kz0 + kMarchPlanes - 1) / kMarchPlanes);
+                DirPtrs<S> ptr;
+                for (int q = 0; q < Q; ++q) {
+                    ptr.src[q] = static_cast<const S *>(src) + (size_t)q * (size_t)a.g.N;
+                    ptr.dst[q] = static_cast<S *>(dst) + (size_t)q * (size_t)a.g.N;
+                }
+                const Phys<float> P = phys(a);
+                const DirConst<float> D = dirs(a);
+                const float *ff = static_cast<const float *>(a.force_field);
+                const float F0 = (float)a.F[0], F1 = (float)a.F[1], F2 = (float)a.F[2];
+                const bool sr = a.sr_key != 0, yzw = a.g.wall[1] || a.g.wall[2];
+                if (sr && yzw)
+                    k_step_march<ST, LB_CORR_LOCAL, true, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
+                                                                                              F2, ff, a.sr_key);
+                else if (sr)
+                    k_step_march<ST, LB_CORR_LOCAL, true, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
+                                                                                               F2, ff, a.sr_key);
+                else if (yzw)
+                    k_step_march<ST, LB_CORR_LOCAL, false, true><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0, F1,
+                                                                                               F2, ff, 0u);
+                else
+                    k_step_march<ST, LB_CORR_LOCAL, false, false><<<grid, block, 0, a.stream>>>(ptr, a.g, P, D, F0,
+                                                                                                F1, F2, ff, 0u);
+                return cudaGetLastError();
+            }
+        }
         constexpr int ZC = kPairPlanes;
         const int np = a.g.nx / 2;
         int bx = kBlockX;
@@ -438,6 +480,9 @@ const char *Ops<ST>::step_kernel_name(const LaunchArgs &a)
         const int minb = (wide && !small) ? 1 : (!wide && small ? LBC_BULK16_MINBLOCKS : 2);
         snprintf(buf, sizeof(buf), "k_step_bulk<%s,%s,%d,%d,%d>", storage_name(ST), corr_name(a.corr), nxmax, ns,
                  minb);
+    } else if (use_march(a)) {
+        snprintf(buf, sizeof(buf), "k_step_march<%s,%s,%d,%s,%s>", storage_name(ST), corr_name(a.corr), kMarchPlanes,
+                 a.sr_key != 0 ? "true" : "false", (a.g.wall[1] || a.g.wall[2]) ? "walls" : "periodic");
     } else if (use_pair(a)) {
         const bool yzw = a.g.wall[1] || a.g.wall[2] || a.model == 1 ||
                          (a.corr != LB_CORR_LOCAL && a.corr != LB_CORR_FULL);

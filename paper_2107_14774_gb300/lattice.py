@@ -37,7 +37,8 @@ class Lattice:
     BF16, FP32 arithmetic).  corr: "none", "lowmach", "local", "full".
     walls: any of "x", "y", "z" (half-way bounce-back walls normal to that axis).
     kernel: "auto" (two-node kernel where possible), "one" (one node per thread), "pair" (two
-    nodes per thread) or "staged" (rows staged in shared memory by bulk copies).
+    nodes per thread), "staged" (rows staged in shared memory by bulk copies) or "march" (two
+    nodes per thread marching along z, the next plane's sources staged in shared memory).
     rounding: "nearest" or "stochastic" (FP16/BF16 storage only).
     model: "central" (3DCCM) or "raw" (3DCRM: raw moments relaxed with the same corrected
     equilibria; LOCAL corrections only).
@@ -61,7 +62,7 @@ class Lattice:
         cfg.force = (ctypes.c_double * 3)(*force)
         cfg.lid_u = lid_u
         cfg.stream = s.cuda_stream
-        cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3}[kernel]
+        cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3, "march": 4}[kernel]
         cfg.rounding = {"nearest": 0, "stochastic": 1}[rounding]
         cfg.rounding_seed = rounding_seed
         cfg.model = {"central": 0, "raw": 1}[model]
@@ -224,6 +225,11 @@ class Lattice:
     def set_rates(self, omega_nu: float, omega_xi: float):
         """lb_set_rates: relaxation rates directly (0 < omega < 2)."""
         check(self.lib.lb_set_rates(self.ctx, float(omega_nu), float(omega_xi)))
+        return self
+
+    def set_lid(self, lid_u: float):
+        """lb_set_lid: lid velocity (x velocity of the wall at the top in y) for the following steps."""
+        check(self.lib.lb_set_lid(self.ctx, float(lid_u)))
         return self
 
     def objective_ke(self) -> float:

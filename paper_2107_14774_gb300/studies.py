@@ -30,16 +30,24 @@ def lid_cavity(nx, ny, nz, r, s, cs2, U, omega_nu, omega_xi=1.0, model="central"
     return lat
 
 
-def survives(lat, steps, check_every=5000) -> bool:
+def survives(lat, steps, check_every=5000, lid_u=0.0, ramp_steps=0, ramp_every=100) -> bool:
     """Run up to `steps` steps, stopping at the first check that finds a non-positive or
-    non-finite density."""
+    non-finite density.  With ramp_steps > 0 the lid starts at rest and its velocity rises
+    linearly to lid_u over the first ramp_steps steps (updated every ramp_every steps)."""
     done = 0
     while done < steps:
-        k = min(check_every, steps - done)
+        if ramp_steps and done < ramp_steps:
+            lat.set_lid(lid_u * min(1.0, (done + ramp_every) / ramp_steps))
+            k = min(ramp_every, steps - done)
+        else:
+            if ramp_steps:
+                lat.set_lid(lid_u)
+            k = min(check_every - done % check_every, steps - done)
         lat.step(k)
         done += k
-        if not lat.is_stable():
-            return False
+        if done % check_every == 0 or done == steps:
+            if not lat.is_stable():
+                return False
     return True
 
 
@@ -58,13 +66,14 @@ def bisect(stable, lo, hi, tol):
 
 
 def max_stable_lid_velocity(nx, ny, nz, r, s, cs2, omega_nu, omega_xi=1.0, model="central", steps=100_000,
-                            u_hi=0.6, tol=0.005, storage="f32", corr="local"):
+                            u_hi=0.6, tol=0.005, storage="f32", corr="local", ramp_steps=0):
     """Sec. 7 stability test: the largest lid velocity U (to within tol) for which the
-    cavity stays stable for `steps` steps."""
+    cavity stays stable for `steps` steps (the lid started impulsively, or brought up to U
+    linearly over ramp_steps steps)."""
     def stable(U):
         lat = lid_cavity(nx, ny, nz, r, s, cs2, U, omega_nu, omega_xi, model, storage, corr)
         try:
-            return survives(lat, steps)
+            return survives(lat, steps, lid_u=U, ramp_steps=ramp_steps)
         finally:
             lat.close()
     return bisect(stable, 0.0, u_hi, tol)

@@ -439,6 +439,45 @@ def test_moving_lid_parity(oracle_mod):
     lat.close()
 
 
+@pytest.mark.parametrize("own_stream", [False, True])
+def test_lid_velocity_changed_between_steps(oracle_mod, own_stream):
+    """lb_set_lid between lb_step calls (a lid ramp): the step from t to t + 1 uses the lid
+    set before the call that runs it, as in the oracle with its lid changed between the
+    same steps (Eq. 69).  On a stream of its own the 70-step segment replays CUDA graphs."""
+    from paper_2107_14774_gb300 import Lattice
+    n, r, s = (10, 12, 8), 0.5, 0.75
+    rho, u = np.ones(n[::-1]), np.zeros((3,) + n[::-1])
+    lat = Lattice(*n, r_y=r, r_z=s, nu=0.02, cs2=0.04, storage="f64", walls="xyz", lid_u=0.03,
+                  stream=torch.cuda.Stream() if own_stream else None)
+    p = lat.params
+    o = oracle_mod.Oracle(*n, r=r, s=s, cs2=p["cs2"], omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
+                          corr=oracle_mod.CORR_LOCAL, walls="xyz", lid_u=0.03)
+    lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    f = o.init(rho, u)
+    for lid, steps in ((0.03, 5), (0.06, 3), (0.08, 70 if own_stream else 9), (0.0, 4), (0.05, 1)):
+        lat.set_lid(lid).step(steps)
+        o.p.lid_u = lid
+        f = o.run(f, steps)
+        assert rel(lat.populations().cpu().numpy(), f) < TOL64
+    lat.close()
+
+
+def test_lid_requires_y_walls():
+    """lb_set_lid refuses a moving lid without walls normal to y and a non-finite value;
+    a lid at rest is accepted on any lattice."""
+    from paper_2107_14774_gb300 import Lattice, LBError
+    lat = Lattice(8, 8, 8, nu=0.02, walls="z")
+    lat.set_lid(0.0)
+    with pytest.raises(LBError, match="walls normal to y"):
+        lat.set_lid(0.1)
+    lat.close()
+    lat = Lattice(8, 8, 8, nu=0.02, walls="y")
+    with pytest.raises(LBError, match="non-finite"):
+        lat.set_lid(float("nan"))
+    lat.set_lid(0.1)
+    lat.close()
+
+
 def test_unstable_state_is_reported():
     """A NaN planted in the initial density is reported by lb_reduce as LB_EUNSTABLE."""
     from paper_2107_14774_gb300 import Lattice, LBError
@@ -465,7 +504,7 @@ def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
     rho, u = synth.solenoidal_random(*n, r, s, 3.0, 0.03, seed=21)
     ff = synth.force_field(*n, 1e-5, seed=22)
     out = {}
-    for kern in ("auto", "pair", "one", "staged"):
+    for kern in ("auto", "pair", "one", "staged", "march"):
         lat = Lattice(*n, r_y=r, r_z=s, nu=0.01, storage=storage, walls=walls, force=(1e-6, 0, 0), kernel=kern)
         lat.set_force_field(torch.from_numpy(ff).cuda())
         lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(8)
@@ -477,8 +516,34 @@ def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
     _, ur = o.moments(o.run(o.init(rho, u), 8))
     for kern in out:
         assert rel(out[kern], ur) < tol, kern
-    for kern in ("auto", "pair", "staged"):
+    for kern in ("auto", "pair", "staged", "march"):
         assert rel(out[kern], out["one"]) < tol, kern
+
+
+@pytest.mark.parametrize("n", [(160, 6, 13), (66, 5, 9), (64, 4, 8)])
+@pytest.mark.parametrize("walls", ["", "y", "z", "yz"])
+@pytest.mark.parametrize("storage,rounding", [("bf16s", "nearest"), ("f16s", "nearest"), ("bf16s", "stochastic"),
+                                              ("f16s", "stochastic")])
+def test_march_kernel_matches_pair_bit_for_bit(storage, rounding, walls, n):
+    """The z-marching kernel (sources of the next plane staged in shared memory) computes
+    what the two-node kernel computes from the same words: the stored state is equal bit
+    for bit after several steps, on rows that end inside a warp (80 and 33 node pairs: a
+    segment whose only lane is both first and last), rows of exactly one segment, partial
+    blocks in y, plane counts that are not a multiple of the marching depth, walls,
+    stochastic rounding and a per-node force field."""
+    from paper_2107_14774_gb300 import Lattice
+    rho, u = synth.solenoidal_random(*n, 0.5, 1.0, 2.0, 0.03, seed=31)
+    ff = synth.force_field(*n, 1e-5, seed=32)
+    states = {}
+    for kern in ("pair", "march"):
+        lat = Lattice(*n, r_y=0.5, r_z=1.0, nu=0.01, storage=storage, walls=walls, kernel=kern, rounding=rounding,
+                      rounding_seed=3)
+        lat.set_force_field(torch.from_numpy(ff).cuda())
+        lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(5)
+        assert lat.step_kernel.startswith("k_step_march<" if kern == "march" else "k_step_pair<"), lat.step_kernel
+        states[kern] = lat.get_state().cpu()
+        lat.close()
+    assert torch.equal(states["march"], states["pair"])
 
 
 @pytest.mark.parametrize("kern", ["auto", "one", "staged"])

@@ -20,6 +20,44 @@ def test_bisect_finds_monotone_threshold():
     assert bisect(lambda v: False, 0.0, 0.4, 0.005) < 0.005
 
 
+class _Recorder:
+    """Stands in for a Lattice: records lid changes and step counts; never unstable."""
+
+    def __init__(self):
+        self.log, self.t = [], 0
+
+    def set_lid(self, u):
+        self.log.append(("lid", self.t, u))
+        return self
+
+    def step(self, k):
+        self.t += k
+        self.log.append(("step", k))
+        return self
+
+    def is_stable(self):
+        self.log.append(("check", self.t))
+        return True
+
+
+def test_survives_ramps_the_lid_then_holds_it():
+    """With a ramp the lid rises linearly to U in equal increments over ramp_steps steps and
+    then stays at U; the stability checks fall on multiples of check_every and at the end."""
+    from paper_2107_14774_gb300.studies import survives
+    lat = _Recorder()
+    assert survives(lat, 1250, check_every=500, lid_u=0.2, ramp_steps=400, ramp_every=100)
+    lids = [(t, u) for kind, t, u in (e for e in lat.log if e[0] == "lid")]
+    assert [t for t, _ in lids[:4]] == [0, 100, 200, 300]
+    assert np.allclose([u for _, u in lids[:4]], [0.05, 0.1, 0.15, 0.2])
+    assert all(u == 0.2 for _, u in lids[4:])
+    assert lat.t == 1250
+    assert [e[1] for e in lat.log if e[0] == "check"] == [500, 1000, 1250]
+    plain = _Recorder()
+    assert survives(plain, 1250, check_every=500)
+    assert not any(e[0] == "lid" for e in plain.log)
+    assert [e[1] for e in plain.log if e[0] == "step"] == [500, 500, 250]
+
+
 @pytest.mark.gpu
 def test_stability_driver_small():
     """A tiny cavity: a lid at rest-like speed survives, the bisected threshold lies inside
