@@ -320,23 +320,33 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
             if j >= 0:
                 lats[j % D].moments(*outs[j % D])              # download of step j, waits for it
 
-    # the host link alone: one step's bytes up and down at once, no compute
+    # the host link alone, without the library: one step's bytes up, down, and both at once
     up = (torch.empty(rho_h.shape, dtype=rho_h.dtype, device=dev), torch.empty(u_h.shape, dtype=u_h.dtype, device=dev))
     down = (torch.zeros_like(up[0]), torch.zeros_like(up[1]))
+    side = torch.cuda.Stream(dev)
 
-    def link(n):
-        for _ in range(n):
-            with torch.cuda.stream(streams[0]):
-                up[0].copy_(rho_h, non_blocking=True)
-                up[1].copy_(u_h, non_blocking=True)
-            with torch.cuda.stream(streams[-1] if D > 1 else torch.cuda.Stream(dev)):
-                outs[0][0].copy_(down[0], non_blocking=True)
-                outs[0][1].copy_(down[1], non_blocking=True)
-            torch.cuda.synchronize(dev)
+    def h2d():
+        with torch.cuda.stream(streams[0]):
+            up[0].copy_(rho_h, non_blocking=True)
+            up[1].copy_(u_h, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(side):
+            outs[0][0].copy_(down[0], non_blocking=True)
+            outs[0][1].copy_(down[1], non_blocking=True)
+
+    def copies(*fns):
+        def run(n):
+            for _ in range(n):
+                for f in fns:
+                    f()
+                torch.cuda.synchronize(dev)
+        return run
 
     timings = {}
-    for name, fn in (("serial", serial), ("pipelined", pipelined), ("link", link)):
-        fn(2)
+    for name, fn in (("serial", serial), ("pipelined", pipelined), ("h2d", copies(h2d)), ("d2h", copies(d2h)),
+                     ("both", copies(h2d, d2h))):
+        fn(D + 1)                                      # every context has staged and stepped once
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -346,6 +356,7 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
     for lat in lats:
         lat.close()
     del up, down
+    per_step = {k: 1e3 * v / e2e_steps for k, v in timings.items()}
     e2e = {"value": aggregate_mlups(N, e2e_steps, world, timings["pipelined"]), "unit": "MLUPS",
            "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N, "contexts": D,
            "what": f"per step: lb_init from pinned host rho,u + lb_step(1) + lb_moments to pinned host; {D} "
@@ -353,9 +364,11 @@ def run_e2e(args, rho, u, dims, stream, dev, world, barrier):
                    "download and compute of the steps before it)",
            "serial": {"value": aggregate_mlups(N, e2e_steps, world, timings["serial"]), "unit": "MLUPS",
                       "what": "the same with one context, each step's copies and step in sequence"},
-           "link_bound": {"value": aggregate_mlups(N, e2e_steps, world, timings["link"]), "unit": "MLUPS",
-                          "what": "the same bytes copied between pinned host and device memory, both directions "
-                                  "at once, without the library"}}
+           "link_ms_per_step": {"h2d": per_step["h2d"], "d2h": per_step["d2h"], "both_at_once": per_step["both"]},
+           "link_bound": {"value": aggregate_mlups(N, e2e_steps, world, max(timings["h2d"], timings["d2h"])),
+                          "unit": "MLUPS",
+                          "what": "the full-duplex bound: one step's bytes in the slower direction alone, pinned "
+                                  "host <-> device copies without the library"}}
     e2e["link_frac"] = e2e["value"] / e2e["link_bound"]["value"]
     return e2e
 
@@ -498,33 +511,38 @@ def run_study(args):
                 emit(rec)
             lat.close()
             torch.cuda.empty_cache()
-    elif args.study == "adjoint":          # discrete adjoint, 128x64x64, T = 500, K = 50, FP32
+    elif args.study == "adjoint":          # discrete adjoint, 128x64x64, T = 500, K = 50 and K = 1, FP32
         import torch
         from paper_2107_14774_gb300 import Lattice
-        n, T, K = (128, 64, 64), 500, 50
+        n, T = (128, 64, 64), 500
         rho, u = synth.solenoidal_random(*n, 1.0, 0.5, 4.0, 0.01, seed=4)
         ff = synth.force_field(*n, 1e-5, seed=44)
         lat = Lattice(*n, r_y=1.0, r_z=0.5, nu=0.01, storage="f32", stream=torch.cuda.Stream())
         lat.set_force_field(torch.from_numpy(ff).cuda())
         N = n[0] * n[1] * n[2]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        for rep in range(2):                      # the first call also allocates the checkpoints
-            lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
-            torch.cuda.synchronize()
-            ev[0].record(lat.stream)
-            J, dJdF, dJdw = lat.adjoint_ke(T, K)
-            ev[1].record(lat.stream)
-            torch.cuda.synchronize()
         lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
         torch.cuda.synchronize()
         ev[2].record(lat.stream)
         lat.step(T)
         ev[3].record(lat.stream)
         torch.cuda.synchronize()
-        t_adj, t_fwd = ev[0].elapsed_time(ev[1]) / 1e3, ev[2].elapsed_time(ev[3]) / 1e3
-        emit({"study": "adjoint", "grid": list(n), "T": T, "K": K, "J": J, "dJ_domega": list(dJdw),
-              "seconds_adjoint_total": t_adj, "seconds_forward_T_steps": t_fwd, "ratio": t_adj / t_fwd,
-              "node_steps_per_s": N * T / t_adj})
+        t_fwd = ev[2].elapsed_time(ev[3]) / 1e3
+        # K = 50: checkpoints every 50 steps, each segment recomputed once; K = 1: all 500
+        # states resident (28 GB), nothing recomputed
+        for K in (50, 1):
+            for rep in range(2):                  # the first call also pages in the allocations
+                lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+                torch.cuda.synchronize()
+                ev[0].record(lat.stream)
+                J, dJdF, dJdw = lat.adjoint_ke(T, K)
+                ev[1].record(lat.stream)
+                torch.cuda.synchronize()
+            t_adj = ev[0].elapsed_time(ev[1]) / 1e3
+            emit({"study": "adjoint", "grid": list(n), "T": T, "K": K, "J": J, "dJ_domega": list(dJdw),
+                  "seconds_adjoint_total": t_adj, "seconds_forward_T_steps": t_fwd, "ratio": t_adj / t_fwd,
+                  "node_steps_per_s": N * T / t_adj,
+                  "stored_states": (T + K - 1) // K + K - 1})
         lat.close()
     else:                                  # Sec. 6: shallow cavity, cubic vs cuboid, Re = 100, Ma = 0.1
         cubic = studies.shallow_cavity(256, 64, 128, 1.0, 1.0, 1 / 3, 0.1 * (1 / 3) ** 0.5)
@@ -568,7 +586,7 @@ def main():
                          "stability / xi = Sec. 7 Figs. 8 / 9, reynolds = Fig. 10, cavity = Sec. 6, "
                          "adjoint = timing of the checkpointed adjoint on the 128x64x64 case, "
                          "channel = 768x192x384 channel run of reduced-precision storage against FP32")
-    ap.add_argument("--e2e-contexts", type=int, default=3,
+    ap.add_argument("--e2e-contexts", type=int, default=2,
                     help="contexts taking the end-to-end steps in turn (1: no overlap)")
     ap.add_argument("--study-corr", default="full,local,none",
                     help="correction modes of the omega_xi study (Fig. 9)")

@@ -219,9 +219,12 @@ lb_status lb_objective_ke(lb_ctx *ctx, double *J);
  * dJ/dF [3][N] (real; the gradient with respect to the per-node body force field,
  * i.e. to the total force at each node) and dJ/domega = (dJ/domega_nu,
  * dJ/domega_xi) on the host.  The forward states are kept every K steps
- * (checkpoints) and each K-step segment is recomputed once during the backward
- * sweep, so device memory grows as (ceil(T/K) + K) stored states; the temporary
- * buffers are allocated and freed inside the call.  On return the context holds
+ * (checkpoints, written there by the step kernels themselves) and each K-step segment
+ * is recomputed once during the backward sweep, so device memory grows as
+ * (ceil(T/K) + K - 1) stored states of lb_state_bytes each.  K = 1 keeps all T states
+ * resident and recomputes nothing (a 128x64x64 FP32 lattice takes 57 MB per state).
+ * These work buffers are allocated by the first call that needs them and kept by the
+ * context for later calls (grown when a call needs more); lb_destroy frees them.  On return the context holds
  * the state after the T steps (as after lb_step(ctx, T)).  Corrections NONE,
  * LOWMACH or LOCAL; no moving lid (LB_EINVAL otherwise).  Synchronises. */
 lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2], double *J);

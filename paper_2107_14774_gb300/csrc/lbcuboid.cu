@@ -87,6 +87,10 @@ struct lb_ctx {
     // streams that state, and the moving-wall term of that streaming belongs to the
     // same step (so a lid changed between lb_step calls acts from the next step on).
     double lid_state;
+    // Work buffers of lb_adjoint_ke (checkpoints, segment, adjoint fields, block sums),
+    // kept for the next call and grown when a call needs more; freed by lb_destroy
+    void *adj_buf[7];
+    size_t adj_bytes[7];
     int *err;               // error word of the bounded waits of the staged kernel
     int sm_count;
     // CUDA graphs of kGraphSteps consecutive steps starting from buffer 0 / 1, with
@@ -613,6 +617,7 @@ void lb_destroy(lb_ctx *c)
     cudaFree(c->out4);
     cudaFree(c->status);
     cudaFree(c->err);
+    for (int b = 0; b < 7; ++b) cudaFree(c->adj_buf[b]);
     drop_graph(c, 0);
     drop_graph(c, 1);
     for (int s = 0; s < kMaxSub; ++s)
@@ -858,6 +863,24 @@ struct Scratch {
     }
 };
 
+// Work buffer `slot` of lb_adjoint_ke with at least `bytes` bytes (reused across calls).
+cudaError_t adjoint_buffer(lb_ctx *c, int slot, size_t bytes, void **p)
+{
+    if (c->adj_bytes[slot] < bytes) {
+        cudaError_t e = cudaFree(c->adj_buf[slot]);
+        c->adj_buf[slot] = nullptr;
+        c->adj_bytes[slot] = 0;
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMalloc(&c->adj_buf[slot], bytes)) != cudaSuccess) {
+            c->adj_buf[slot] = nullptr;
+            return e;
+        }
+        c->adj_bytes[slot] = bytes;
+    }
+    *p = c->adj_buf[slot];
+    return cudaSuccess;
+}
+
 lb_status sum_pairs(lb_ctx *c, const double *dev, long long nblocks, double out[2])
 {
     std::vector<double> h(2 * (size_t)nblocks);
@@ -907,50 +930,63 @@ lb_status lb_adjoint_ke(lb_ctx *c, int T, int K, void *dJdF, double dJdomega[2],
     const long long N = c->g.N;
     const int nck = (T + K - 1) / K;
     const long long nb = adjoint_blocks(c->g);
-    Scratch s;
     char *ck = nullptr, *seg = nullptr;
     void *lam[2] = {nullptr, nullptr}, *dF = nullptr;
     double *jpart = nullptr, *wpart = nullptr;
-    LB_CUDA(s.alloc((void **)&ck, (size_t)nck * sb));
-    LB_CUDA(s.alloc((void **)&seg, (size_t)K * sb));
-    LB_CUDA(s.alloc(&lam[0], (size_t)Q * N * c->rbytes));
-    LB_CUDA(s.alloc(&lam[1], (size_t)Q * N * c->rbytes));
-    LB_CUDA(s.alloc(&dF, 3 * (size_t)N * c->rbytes));
-    LB_CUDA(s.alloc((void **)&jpart, 2 * nb * sizeof(double)));
-    LB_CUDA(s.alloc((void **)&wpart, 2 * nb * sizeof(double)));
+    LB_CUDA(adjoint_buffer(c, 0, (size_t)nck * sb, (void **)&ck));
+    if (K > 1) LB_CUDA(adjoint_buffer(c, 1, (size_t)(K - 1) * sb, (void **)&seg));
+    LB_CUDA(adjoint_buffer(c, 2, (size_t)Q * N * c->rbytes, &lam[0]));
+    LB_CUDA(adjoint_buffer(c, 3, (size_t)Q * N * c->rbytes, &lam[1]));
+    LB_CUDA(adjoint_buffer(c, 4, 3 * (size_t)N * c->rbytes, &dF));
+    LB_CUDA(adjoint_buffer(c, 5, 2 * nb * sizeof(double), (void **)&jpart));
+    LB_CUDA(adjoint_buffer(c, 6, 2 * nb * sizeof(double), (void **)&wpart));
     LB_CUDA(cudaMemsetAsync(jpart, 0, 2 * nb * sizeof(double), c->stream));
     LB_CUDA(cudaMemsetAsync(wpart, 0, 2 * nb * sizeof(double), c->stream));
     const int storage = c->cfg.storage;
-
-    // forward sweep with a checkpoint every K steps
-    for (int n = 0; n < T; ++n) {
-        if (n % K == 0)
-            LB_CUDA(cudaMemcpyAsync(ck + (size_t)(n / K) * sb, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice,
-                                    c->stream));
-        lb_status st = lb_step(c, 1);
-        if (st) return st;
-    }
     const LaunchArgs a = launch_args(c);
-    {
-        const void *src = c->buf[c->cur];
-        LB_CUDA(dispatch(storage, [&](auto ops) { return decltype(ops)::adjoint_seed(a, src, lam[0], dF, jpart); }));
+    auto step = [&](const void *src, void *dst) {
+        return dispatch(storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); });
+    };
+
+    // forward sweep: state 0 is copied into checkpoint 0; each step writes the next state
+    // straight into its checkpoint slot (states K, 2K, ...) or into the context's two
+    // buffers, which end up holding state T as lb_step(T) would leave it.  With K = 1 all
+    // states stay resident and nothing is recomputed below.
+    LB_CUDA(cudaMemcpyAsync(ck, c->buf[c->cur], sb, cudaMemcpyDeviceToDevice, c->stream));
+    const void *src = ck;
+    int w = 0;
+    for (int n = 0; n < T; ++n) {
+        void *dst;
+        if ((n + 1) % K == 0 && (n + 1) / K < nck) {
+            dst = ck + (size_t)((n + 1) / K) * sb;
+        } else {
+            dst = c->buf[w];
+            w ^= 1;
+        }
+        LB_CUDA(step(src, dst));
+        src = dst;
     }
-    // backward sweep: recompute each segment from its checkpoint, then walk it back
+    c->cur = (src == c->buf[0]) ? 0 : 1;   // the last step always writes a context buffer
+    c->t += T;
+    c->fresh = false;
+    c->lid_state = c->cfg.lid_u;
+    LB_CUDA(dispatch(storage, [&](auto ops) {
+        return decltype(ops)::adjoint_seed(a, c->buf[c->cur], lam[0], dF, jpart);
+    }));
+    // backward sweep: recompute each segment's states n0 + 1 .. n1 - 1 from its
+    // checkpoint (state n0), then walk the segment back
     int li = 0;
     for (int sgm = nck - 1; sgm >= 0; --sgm) {
         const int n0 = sgm * K, n1 = std::min(T, n0 + K);
-        LB_CUDA(cudaMemcpyAsync(seg, ck + (size_t)sgm * sb, sb, cudaMemcpyDeviceToDevice, c->stream));
-        for (int i = 1; i < n1 - n0; ++i) {
-            const void *src = seg + (size_t)(i - 1) * sb;
-            void *dst = seg + (size_t)i * sb;
-            LB_CUDA(dispatch(storage, [&](auto ops) { return decltype(ops)::step(a, src, dst); }));
-        }
+        const char *base = ck + (size_t)sgm * sb;
+        auto state = [&](int n) -> const void * { return n == n0 ? base : seg + (size_t)(n - n0 - 1) * sb; };
+        for (int n = n0 + 1; n < n1; ++n) LB_CUDA(step(state(n - 1), seg + (size_t)(n - n0 - 1) * sb));
         for (int n = n1 - 1; n >= n0; --n) {
-            const void *src = seg + (size_t)(n - n0) * sb;
+            const void *sn = state(n);
             const void *lin = lam[li];
             void *lout = lam[li ^ 1];
             LB_CUDA(dispatch(storage, [&](auto ops) {
-                return decltype(ops)::adjoint_step(a, src, lin, lout, dF, wpart);
+                return decltype(ops)::adjoint_step(a, sn, lin, lout, dF, wpart);
             }));
             li ^= 1;
         }

@@ -91,6 +91,39 @@ def test_adjoint_leaves_state_after_T_steps():
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("walls", ["", "y"])
+def test_adjoint_independent_of_checkpoint_interval(storage, walls):
+    """Every checkpoint interval K gives the same J, dJ/dF and dJ/domega bit for bit: the
+    adjoint steps read the same states in the same order whether they were kept (K = 1
+    keeps every state resident and recomputes nothing) or recomputed from a checkpoint
+    (K >= T recomputes the whole run from the initial state); and every K leaves the
+    state lb_step(T) leaves."""
+    from paper_2107_14774_gb300 import Lattice
+    n, T = (16, 8, 8), 13
+    rho, u, ff = _tiny_setup(n, 1.0, 0.5)
+
+    def fresh():
+        lat = Lattice(*n, r_y=1.0, r_z=0.5, nu=0.01, storage=storage, walls=walls)
+        lat.set_force_field(torch.from_numpy(ff).cuda())
+        lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+        return lat
+    ref = fresh()
+    ref.step(T)
+    state_T = ref.get_state().cpu()
+    ref.close()
+    out = {}
+    for K in (1, 3, 5, 13, 20):
+        lat = fresh()
+        J, g, w = lat.adjoint_ke(T, K)
+        assert torch.equal(lat.get_state().cpu(), state_T) and lat.time_step == T, K
+        out[K] = (J, g.cpu(), w)
+        lat.close()
+    J1, g1, w1 = out[1]
+    for K, (J, g, w) in out.items():
+        assert J == J1 and torch.equal(g, g1) and w == w1, K
+
+
 def test_adjoint_128x64x64_against_central_differences():
     """Adjoint case 128x64x64 periodic, r_z=0.5, FP32, mean kinetic energy after T=500
     steps, checkpoint every 50; u0 from the solenoidal generator at u_rms=0.01 (seed 4),

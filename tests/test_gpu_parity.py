@@ -382,6 +382,44 @@ def test_full_size_decaying_512x256x256_sampled_nodes(oracle_mod, storage):
     assert abs(m1[0] / m0[0] - 1) < 1e-6
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16s"])
+def test_lattice_beyond_32bit_offsets_sampled_nodes(oracle_mod, storage):
+    """A 1024x512x328 lattice holds 27 N = 4.64e9 > 2^32 populations per buffer, so the
+    two-node kernel (32-bit element offsets) gives way to the one-node kernel with 64-bit
+    offsets.  One fused step from a smooth field (three Fourier modes, built on the
+    device), checked at sampled nodes against the oracle's collision of the GPU's own
+    stored values: the last node and the highest plane included, whose populations sit
+    beyond element 2^32 of the buffer.  Mass (FP64 sum over every node) is conserved to
+    1e-6."""
+    from paper_2107_14774_gb300 import Lattice
+    n, r, s, cs2, nu = (1024, 512, 328), 0.5, 1.0, 1 / 12, 0.01
+    assert 27 * n[0] * n[1] * n[2] > 2 ** 32
+    lat = Lattice(*n, r_y=r, r_z=s, nu=nu, cs2=cs2, storage=storage)
+    assert lat.step_kernel.startswith("k_step<"), lat.step_kernel
+    ax = [torch.arange(m, device="cuda", dtype=torch.float32) * (2 * np.pi / m) for m in n]
+    X, Y, Z = ax[0][None, None, :], ax[1][None, :, None], ax[2][:, None, None]
+    rho = 1.0 + 1e-3 * torch.cos(X + Z) * torch.ones_like(Y)
+    u = torch.stack([0.02 * torch.sin(X) * torch.cos(Y) * torch.cos(Z),
+                     -0.01 * torch.cos(X) * torch.sin(Y) * torch.cos(Z),
+                     0.005 * torch.sin(2 * Z) * torch.cos(X) * torch.ones_like(Y)])
+    lat.init(rho, u)
+    del rho, u, X, Y, Z
+    lat.step(1)
+    m0 = lat.reduce()
+    p = lat.params
+    o = oracle_mod.Oracle(r=r, s=s, cs2=cs2, omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
+                          storage_emulation="bf16s" if storage == "bf16s" else None)
+    rng = np.random.default_rng(9)
+    pts = [(0, 0, 0), (n[0] - 1, n[1] - 1, n[2] - 1), (511, 255, n[2] - 1), (n[0] - 1, 0, n[2] - 2)] + [
+        tuple(int(rng.integers(0, m)) for m in n) for _ in range(8)]
+    worst = sampled_step_errors(lat, o, n, pts, storage)
+    m1 = lat.reduce()
+    lat.close()
+    print(storage, "worst", worst)
+    assert worst < (1e-5 if storage == "f32" else 1.0 + 1e-9)
+    assert abs(m1[0] / m0[0] - 1) < 1e-6
+
+
 def test_state_checkpoint_resume_is_bit_exact():
     from paper_2107_14774_gb300 import Lattice
     n = (24, 16, 8)
