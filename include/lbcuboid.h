@@ -275,7 +275,7 @@ lb_status lb_reduce_populations_noalloc(const void *f, int real_size, long long 
                                         const double force[3], double out[4], void *stream);
 
 /* Name (with template arguments) of the step kernel lb_step launches for this
- * context, e.g. "k_step_pair<F32,LOCAL,1,false>"; thread-local storage, valid
+ * context, e.g. "k_step_pair<F32,LOCAL,1,false,periodic>"; thread-local storage, valid
  * until the next call on the same thread.  No counterpart in the paper. */
 const char *lb_step_kernel(const lb_ctx *ctx);
 
