@@ -577,7 +577,7 @@ def main():
                          "bf16s+sr / f16s+sr: stochastic rounding)")
     ap.add_argument("--workload", default="decaying", choices=sorted(WORKLOADS),
                     help="decaying: 512x256x256 periodic (default); channel: 768x192x384 with y walls")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged", "march"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "pair", "one", "staged", "march", "onepass"],
                     help="kernel selection passed to the library (auto = two nodes per thread where possible)")
     ap.add_argument("--dims", default=None,
                     help="NX,NY,NZ override of the lattice size (profiling of a smaller case only)")

@@ -106,7 +106,10 @@ typedef struct {
                               (4- and 2-byte storage, rows of up to 1024 nodes); 4: two nodes per
                               thread marching along z, the next plane's sources copied into
                               shared memory while the current plane is collided (16-bit storage,
-                              LOCAL corrections, rows of at least 64 nodes; else as 0) */
+                              LOCAL corrections, rows of at least 64 nodes; else as 0); 5: FULL
+                              corrections in one pass, the densities of the next plane and of
+                              the tile's halo computed on chip instead of by a pre-pass (lattices
+                              periodic in y and z with rows of a multiple of 64 nodes; else as 0) */
     int model;             /* collision model: 0 = central moments (3DCCM, Sec. 3.2), 1 = raw
                               moments with the same corrected equilibria (3DCRM, Sec. 3.1 raw
                               formulation and Sec. 7); model 1 needs LB_CORR_LOCAL and is not

@@ -514,6 +514,158 @@ k_step_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<
     }
 }
 
+// FULL corrections in one pass (lattices periodic in y and z, rows of a multiple of 64
+// nodes).  A CTA owns a tile of 64 nodes x ROWS rows and marches kFullPlanes planes along
+// z.  Before colliding plane k it computes the densities of plane k + 1 for the tile and
+// its axis halo -- the rows above and below, and the node on either side of each row --
+// into a ring of four density planes in shared memory; the gradient of plane k then
+// comes from the ring (second-order central differences, as in the two-node kernel).
+// Every density is the sum of a node pair's 27 pulled deviations in direction order,
+// exactly as in k_density_pair, so the result equals the two-pass path bit for bit.  A
+// thread's own pair is among the pairs whose density it computes, so the words it pulls
+// for plane k + 1 are parked in its column of a two-plane stash in shared memory and
+// collided from there one iteration later: the populations of a plane are read from
+// HBM once; the halo pulls are served from L2.
+#ifndef LBC_FULL_PLANES
+#define LBC_FULL_PLANES 16
+#endif
+constexpr int kFullPlanes = LBC_FULL_PLANES;
+constexpr int kFullW = 2 * kBlockX + 2;   // the tile's 64 nodes and one on either side
+// Rows per CTA: 8 for 2-byte storage, 4 for 4-byte storage (the stash holds two planes
+// of the CTA's raw words: 55 KB either way, so that three CTAs fit an SM).
+template <int ST>
+__host__ __device__ constexpr int full_rows() { return sizeof(typename Codec<ST>::S) == 2 ? 8 : 4; }
+template <int ST>
+__host__ __device__ constexpr size_t full_smem()
+{
+    return (size_t)4 * (full_rows<ST>() + 2) * kFullW * sizeof(float) +
+           (size_t)2 * Q * full_rows<ST>() * kBlockX * sizeof(typename PairIO<ST>::Raw);
+}
+
+// Pulled words and density of the node pair (i0, i0 + 1) of row j, plane k of a lattice
+// periodic in y and z.
+template <int ST>
+__device__ __forceinline__ F2 pair_pull_density(typename PairIO<ST>::Raw (&raw)[Q],
+                                                const DirPtrs<typename Codec<ST>::S> &ptr, const Geom &g,
+                                                const DirConst<float> &D, int i0, int j, int k)
+{
+    using IO = PairIO<ST>;
+    int ys[3];
+    bool yo[3];
+    axis_sources(j, g.ny, 0, ys, yo);
+    const unsigned nx = (unsigned)g.nx;
+    const unsigned xm = (i0 == 0) ? nx - 1u : (unsigned)i0 - 1u;
+    const unsigned xp = (i0 + 2 == g.nx) ? 0u : (unsigned)i0 + 2u;
+    pair_fetch<ST, false>(raw, ptr, g, i0, xm, xp, ys, yo, k);
+    F2 s(0.f);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) s += IO::dec(raw[a], D.w[a], D.iscale[a]);
+    return F2(1.f) + s;
+}
+
+// Resident CTAs per SM: three of 128 threads for 4-byte storage (168 registers), two of
+// 256 threads for 2-byte storage (128 registers; three would spill).
+template <int ST>
+__host__ __device__ constexpr int full_min_blocks() { return sizeof(typename Codec<ST>::S) == 2 ? 2 : 3; }
+
+template <int ST>
+__global__ void __launch_bounds__(kBlockX * full_rows<ST>(), full_min_blocks<ST>())
+k_step_full(DirPtrs<typename Codec<ST>::S> ptr, Geom g, Phys<float> P, DirConst<float> D, float F0, float F1,
+            float F2s, const float *__restrict__ ff)
+{
+    using IO = PairIO<ST>;
+    using Raw = typename IO::Raw;
+    constexpr int ROWS = full_rows<ST>();
+    constexpr int NT = kBlockX * ROWS;
+    extern __shared__ __align__(16) char full_smem_raw[];
+    // ring of density planes: row 0 = the row above the tile, rows 1..rows = the tile,
+    // row rows + 1 = the row below; column 0 = the node left of the tile, 1..64 the
+    // tile, 65 the node right of it
+    auto R = reinterpret_cast<float (*)[ROWS + 2][kFullW]>(full_smem_raw);
+    // stash[plane & 1][a][thread]: the raw words of each thread's own pair
+    auto stash = reinterpret_cast<Raw (*)[Q][NT]>(full_smem_raw + (size_t)4 * (ROWS + 2) * kFullW * sizeof(float));
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int t = wy * kBlockX + lane;
+    const int i0t = (int)blockIdx.x * 2 * kBlockX;
+    const int j0 = (int)blockIdx.y * ROWS;
+    const int rows = min(ROWS, g.ny - j0);
+    const int k0 = (int)blockIdx.z * kFullPlanes;
+    const int kend = min(k0 + kFullPlanes, g.nz);
+    const int nint = rows * kBlockX, ntask = nint + 2 * kBlockX + 2 * rows;
+
+    // densities of plane kk (periodic in z) into ring slot (kk + 4) & 3; the thread's own
+    // pair (task t < nint: row wy, pair lane) also goes to stash slot kk & 1
+    auto densities = [&](int kk) {
+        const int kw = kk < 0 ? kk + g.nz : (kk >= g.nz ? kk - g.nz : kk);
+        float (*Rs)[kFullW] = R[(kk + 4) & 3];
+        for (int task = t; task < ntask; task += NT) {
+            Raw raw[Q];
+            if (task < nint) {                       // the tile's own pairs
+                const int r = task / kBlockX, p = task % kBlockX;
+                const F2 rho = pair_pull_density<ST>(raw, ptr, g, D, i0t + 2 * p, j0 + r, kw);
+                Rs[1 + r][1 + 2 * p] = rho.v.x;
+                Rs[1 + r][2 + 2 * p] = rho.v.y;
+                if (task == t) {
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) stash[kk & 1][a][t] = raw[a];
+                }
+            } else if (task < nint + 2 * kBlockX) {  // the rows above and below
+                const int h = (task - nint) / kBlockX, p = (task - nint) % kBlockX;
+                int jj = h == 0 ? j0 - 1 : j0 + rows;
+                jj = jj < 0 ? jj + g.ny : (jj >= g.ny ? jj - g.ny : jj);
+                const F2 rho = pair_pull_density<ST>(raw, ptr, g, D, i0t + 2 * p, jj, kw);
+                const int rr = h == 0 ? 0 : rows + 1;
+                Rs[rr][1 + 2 * p] = rho.v.x;
+                Rs[rr][2 + 2 * p] = rho.v.y;
+            } else {                                 // the nodes left and right of each row
+                const int q = task - nint - 2 * kBlockX, r = q / 2, side = q % 2;
+                if (side == 0) {
+                    const int il = i0t == 0 ? g.nx - 2 : i0t - 2;
+                    Rs[1 + r][0] = pair_pull_density<ST>(raw, ptr, g, D, il, j0 + r, kw).v.y;
+                } else {
+                    const int ir = i0t + 2 * kBlockX == g.nx ? 0 : i0t + 2 * kBlockX;
+                    Rs[1 + r][kFullW - 1] = pair_pull_density<ST>(raw, ptr, g, D, ir, j0 + r, kw).v.x;
+                }
+            }
+        }
+    };
+
+    densities(k0 - 1);
+    densities(k0);
+    const int i0 = i0t + 2 * lane, j = j0 + wy;
+    const bool on = wy < rows;
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    const int c = 1 + 2 * lane, r = 1 + wy;
+    for (int k = k0; k < kend; ++k) {
+        densities(k + 1);
+        __syncthreads();   // plane k + 1 complete; planes k - 1 and k were completed before
+        if (on) {
+            F2 h[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) h[a] = IO::dec(stash[k & 1][a][t], D.w[a], D.iscale[a]);
+            const unsigned self = (unsigned)k * nxy + (unsigned)j * nx + (unsigned)i0;
+            F2 Fx(F0), Fy(F1), Fz(F2s);
+            if (ff) {
+                const unsigned N = (unsigned)g.N;
+                Fx += F2(__ldg(reinterpret_cast<const float2 *>(ff + self)));
+                Fy += F2(__ldg(reinterpret_cast<const float2 *>(ff + N + self)));
+                Fz += F2(__ldg(reinterpret_cast<const float2 *>(ff + 2u * N + self)));
+            }
+            const float (*Rc)[kFullW] = R[(k + 4) & 3];
+            const float (*Rm)[kFullW] = R[(k + 3) & 3];
+            const float (*Rp)[kFullW] = R[(k + 5) & 3];
+            const F2 grx = (F2(Rc[r][c + 1], Rc[r][c + 2]) - F2(Rc[r][c - 1], Rc[r][c])) * F2(0.5f * P.ic[0]);
+            const F2 gry = g.ny == 1 ? F2(0.f)
+                                     : (F2(Rc[r + 1][c], Rc[r + 1][c + 1]) - F2(Rc[r - 1][c], Rc[r - 1][c + 1])) *
+                                           F2(0.5f * P.ic[1]);
+            const F2 grz = g.nz == 1 ? F2(0.f)
+                                     : (F2(Rp[r][c], Rp[r][c + 1]) - F2(Rm[r][c], Rm[r][c + 1])) * F2(0.5f * P.ic[2]);
+            collide_pair<LB_CORR_FULL>(h, [&](int a, F2 v) { IO::st2(ptr.dst[a] + self, v, D.w[a], D.scale[a]); },
+                                       P, Fx, Fy, Fz, grx, gry, grz);
+        }
+    }
+}
+
 // Two nodes per thread marching along z, with the sources of the next plane staged in
 // shared memory (16-bit storage).  A warp owns one 64-node segment of row j (32 words,
 // a word being the two 16-bit values of a node pair) and kMarchPlanes consecutive

@@ -507,7 +507,7 @@ lb_status lb_create_ex(const lb_config *cfg, lb_ctx **out)
     if (cfg->storage < LB_F64 || cfg->storage > LB_BF16_SHIFTED) return fail(LB_EINVAL, "lb_create_ex: bad storage");
     if (cfg->corr < LB_CORR_NONE || cfg->corr > LB_CORR_FULL) return fail(LB_EINVAL, "lb_create_ex: bad corr");
     if (cfg->wall_mask & ~7u) return fail(LB_EINVAL, "lb_create_ex: bad wall_mask");
-    if (cfg->kernel < 0 || cfg->kernel > 4) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
+    if (cfg->kernel < 0 || cfg->kernel > 5) return fail(LB_EINVAL, "lb_create_ex: bad kernel selector");
     if (cfg->rounding < 0 || cfg->rounding > 1) return fail(LB_EINVAL, "lb_create_ex: bad rounding mode");
     if (cfg->rounding == 1 && cfg->storage != LB_F16_SHIFTED && cfg->storage != LB_BF16_SHIFTED)
         return fail(LB_EINVAL, "lb_create_ex: stochastic rounding applies to FP16/BF16 storage only");

@@ -37,8 +37,9 @@ class Lattice:
     BF16, FP32 arithmetic).  corr: "none", "lowmach", "local", "full".
     walls: any of "x", "y", "z" (half-way bounce-back walls normal to that axis).
     kernel: "auto" (two-node kernel where possible), "one" (one node per thread), "pair" (two
-    nodes per thread), "staged" (rows staged in shared memory by bulk copies) or "march" (two
-    nodes per thread marching along z, the next plane's sources staged in shared memory).
+    nodes per thread), "staged" (rows staged in shared memory by bulk copies), "march" (two
+    nodes per thread marching along z, the next plane's sources staged in shared memory) or
+    "onepass" (FULL corrections without the density pre-pass).
     rounding: "nearest" or "stochastic" (FP16/BF16 storage only).
     model: "central" (3DCCM) or "raw" (3DCRM: raw moments relaxed with the same corrected
     equilibria; LOCAL corrections only).
@@ -62,7 +63,7 @@ class Lattice:
         cfg.force = (ctypes.c_double * 3)(*force)
         cfg.lid_u = lid_u
         cfg.stream = s.cuda_stream
-        cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3, "march": 4}[kernel]
+        cfg.kernel = {"auto": 0, "one": 1, "pair": 2, "staged": 3, "march": 4, "onepass": 5}[kernel]
         cfg.rounding = {"nearest": 0, "stochastic": 1}[rounding]
         cfg.rounding_seed = rounding_seed
         cfg.model = {"central": 0, "raw": 1}[model]

@@ -75,11 +75,12 @@ def rho_dev_tol(rr, tol, real_size):
     return tol + half_ulp * np.linalg.norm(rr) / np.linalg.norm(rr - 1)
 
 
-@pytest.mark.parametrize("kernel", ["one", "auto"])
+@pytest.mark.parametrize("kernel", ["one", "auto", "onepass"])
 @pytest.mark.parametrize("storage", ["f32", "f32s", "bf16s"])
 @pytest.mark.parametrize("n,r,s,walls", [
     ((37, 12, 9), 0.5, 2.0, ""),          # periodic, ragged x (one node per thread)
     ((38, 12, 9), 0.5, 2.0, ""),          # periodic, even x (two nodes per thread)
+    ((128, 12, 9), 0.5, 1.0, ""),         # periodic, rows of 2 x 64 nodes (single pass)
     ((20, 12, 9), 1.0, 0.5, "y"),         # channel walls (one-sided stencils)
     ((16, 10, 12), 0.5, 1.0, "yz"),       # duct walls
     ((16, 2, 7), 0.5, 1.0, "y"),          # two nodes across the channel: first-order stencil
@@ -105,8 +106,13 @@ def test_fp32_full_corrections_parity(oracle_mod, kernel, storage, n, r, s, wall
     p = lat.params
     o = oracle_mod.Oracle(*n, r=r, s=s, cs2=p["cs2"], omega_nu=p["omega_nu"], omega_xi=p["omega_xi"],
                           corr=oracle_mod.CORR_FULL, walls=walls, force=F)
-    want_pair = kernel == "auto" and n[0] % 2 == 0 and "x" not in walls
-    assert ("k_step_pair" in lat.step_kernel) == want_pair, lat.step_kernel
+    if kernel == "onepass" and n[0] % 64 == 0 and not walls:
+        want = "k_step_full<"
+    elif kernel != "one" and n[0] % 2 == 0 and "x" not in walls:
+        want = "k_step_pair<"
+    else:
+        want = "k_step<"
+    assert lat.step_kernel.startswith(want), lat.step_kernel
     _, _, rg, ug, rr, ur = run_both(lat, o, rho, u, 6)
     p = lat.params
     lat.close()
@@ -556,6 +562,33 @@ def test_kernel_variants_agree(oracle_mod, storage, tol, walls):
         assert rel(out[kern], ur) < tol, kern
     for kern in ("auto", "pair", "staged", "march"):
         assert rel(out[kern], out["one"]) < tol, kern
+
+
+@pytest.mark.parametrize("n", [(128, 16, 40), (64, 12, 17), (192, 1, 20), (64, 2, 1), (64, 9, 33)])
+@pytest.mark.parametrize("storage", ["f32", "f32s", "f16s", "bf16s"])
+def test_full_single_pass_matches_two_pass_bit_for_bit(storage, n):
+    """FULL corrections: the single-pass kernel (densities of the next plane and of the
+    tile's halo computed into a shared-memory ring while marching along z) stores the same
+    state as the density pre-pass plus two-node step, bit for bit, after several steps:
+    tiles cut short in y (12 and 9 rows against 8 per tile) and in z (17, 33 and 40 planes
+    against 16), a lattice one row and one two rows high, a single plane, a force field
+    and density waves along every axis."""
+    from paper_2107_14774_gb300 import Lattice
+    rho, u = synth.solenoidal_random(*n, 0.5, 1.0, 2.0, 0.03, seed=41)
+    rho = (rho + 0.02 * np.cos(2 * np.pi * np.arange(n[0]) / n[0])[None, None, :]
+           + 0.01 * np.sin(2 * np.pi * np.arange(n[1]) / n[1])[None, :, None]
+           + 0.02 * np.sin(2 * np.pi * np.arange(n[2]) / n[2])[:, None, None])
+    ff = synth.force_field(*n, 1e-5, seed=42)
+    states = {}
+    for kern in ("onepass", "auto"):
+        lat = Lattice(*n, r_y=0.5, r_z=1.0, nu=0.02, zeta=0.01, storage=storage, corr="full", kernel=kern,
+                      force=(2e-5, -1e-5, 5e-6))
+        assert lat.step_kernel.startswith("k_step_full<" if kern == "onepass" else "k_step_pair<"), lat.step_kernel
+        lat.set_force_field(torch.from_numpy(ff).cuda())
+        lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()).step(5)
+        states[kern] = lat.get_state().cpu()
+        lat.close()
+    assert torch.equal(states["onepass"], states["auto"])
 
 
 @pytest.mark.parametrize("n", [(160, 6, 13), (66, 5, 9), (64, 4, 8)])
