@@ -530,7 +530,7 @@ def run_study(args):
         t_fwd = ev[2].elapsed_time(ev[3]) / 1e3
         # K = 50: checkpoints every 50 steps, each segment recomputed once; K = 1: all 500
         # states resident (28 GB), nothing recomputed
-        for K in (50, 1):
+        for K in [int(v) for v in args.study_k.split(",")]:
             for rep in range(2):                  # the first call also pages in the allocations
                 lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
                 torch.cuda.synchronize()
@@ -588,6 +588,8 @@ def main():
                          "channel = 768x192x384 channel run of reduced-precision storage against FP32")
     ap.add_argument("--e2e-contexts", type=int, default=2,
                     help="contexts taking the end-to-end steps in turn (1: no overlap)")
+    ap.add_argument("--study-k", default="50,1",
+                    help="adjoint study: checkpoint intervals K to time (1 keeps every state resident)")
     ap.add_argument("--study-corr", default="full,local,none",
                     help="correction modes of the omega_xi study (Fig. 9)")
     ap.add_argument("--study-ramp", type=int, default=0,
