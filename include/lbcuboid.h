@@ -34,6 +34,12 @@
 
 #include <stddef.h>
 
+/* The library is built with hidden symbol visibility; the entry points declared here are
+ * the only symbols it exports. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -287,6 +293,10 @@ const char *lb_last_error(void);
 
 #ifdef __cplusplus
 }
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
 #endif
 
 #endif /* LBCUBOID_H */

@@ -19,7 +19,10 @@ LIB = os.path.join(HERE, "liblbcuboid.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# hidden visibility: only the entry points of include/lbcuboid.h are exported (template
+# statics and helpers stay private to this library even when another build is loaded)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc() -> str:

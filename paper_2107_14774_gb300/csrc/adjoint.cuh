@@ -490,6 +490,120 @@ k_adjoint(const typename Codec<ST>::S *__restrict__ src, const typename Codec<ST
     block_sum2_accumulate(wn_b, wb_b, wpart);
 }
 
+// The adjoint step marching along z (4-byte storage): each thread keeps its (x, y) node
+// and steps through kAdjPlanes planes.  The 27 pulled state words and the 27 transposed
+// lambda words of a plane are copied into the thread's own column of a two-slot shared
+// memory stage by 4-byte cp.async, those of the next plane being issued before the
+// current plane is waited for, so that the loads travel while the per-node VJP (about
+// 2,400 instructions) runs; the force field and the dJ/dF to be updated are loaded into
+// registers ahead of their use.  The same arithmetic as k_adjoint, node by node; only
+// the FP64 partial sums of dJ/domega are summed in another order.
+// Measured on GB300 (lb_adjoint_ke, 128x64x64 with a force field, T = 500, FP32): three
+// CTAs per SM (170 registers, no spill) take the K = 1 call to 41.4 ms against 44.1 ms for
+// k_adjoint; at four CTAs (128 registers, ~90 B spilled) it took 46.7-48.3 ms.  Two or four
+// planes per thread measure alike; eight leave too few CTAs on this lattice.
+#ifndef LBC_ADJ_PLANES
+#define LBC_ADJ_PLANES 4
+#endif
+#ifndef LBC_ADJ_MARCH_MINBLOCKS
+#define LBC_ADJ_MARCH_MINBLOCKS 3
+#endif
+constexpr int kAdjPlanes = LBC_ADJ_PLANES;
+constexpr size_t kAdjStageBytes = (size_t)2 * 2 * Q * kAdjThreads * 4;
+
+template <int ST, int CORR>
+__global__ void __launch_bounds__(kAdjThreads, LBC_ADJ_MARCH_MINBLOCKS)
+k_adjoint_march(const typename Codec<ST>::S *__restrict__ src, const typename Codec<ST>::T *__restrict__ lam_in,
+                typename Codec<ST>::T *__restrict__ lam_out, Geom g, Phys<typename Codec<ST>::T> P,
+                DirConst<typename Codec<ST>::T> D, typename Codec<ST>::T F0, typename Codec<ST>::T F1,
+                typename Codec<ST>::T F2, const typename Codec<ST>::T *__restrict__ ff,
+                typename Codec<ST>::T *__restrict__ dJdF, double *__restrict__ wpart)
+{
+    using C = Codec<ST>;
+    using T = typename C::T;
+    static_assert(sizeof(typename C::S) == 4 && sizeof(T) == 4, "the staged adjoint copies 4-byte words");
+    extern __shared__ __align__(16) unsigned adj_stage[];   // [slot][word][thread], words 0..26 state, 27..53 lambda
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = (int)blockIdx.z * kAdjPlanes;
+    const int kend = min(k0 + kAdjPlanes, g.nz);
+    const long long N = g.N;
+    double wn_b = 0.0, wb_b = 0.0;
+    auto slot = [&](int s, int w) -> unsigned * { return adj_stage + ((size_t)s * 2 * Q + w) * kAdjThreads + tid; };
+    auto issue = [&](int k, int s) {
+        const Pull q = make_pull(g, i, j, k);
+        const unsigned *sw = reinterpret_cast<const unsigned *>(src);
+        const unsigned *lw = reinterpret_cast<const unsigned *>(lam_in);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const int cx = ex(a) + 1, cy = ey(a) + 1, cz = ez(a) + 1;
+            const bool out = q.xo[cx] | q.yo[cy] | q.zo[cz];
+            const long long soff = out ? (long long)opp(a) * N + q.base
+                                       : (long long)a * N + q.zoff[cz] + q.yoff[cy] + q.xs[cx];
+            cp_async4(slot(s, a), sw + soff);
+            const int mx = 1 - ex(a), my = 1 - ey(a), mz = 1 - ez(a);   // the source x + e_a
+            const bool mout = q.xo[mx] | q.yo[my] | q.zo[mz];
+            const long long loff = mout ? (long long)opp(a) * N + q.base
+                                        : (long long)a * N + q.zoff[mz] + q.yoff[my] + q.xs[mx];
+            cp_async4(slot(s, Q + a), lw + loff);
+        }
+        cp_async_commit();
+    };
+    if (i < g.nx && j < g.ny) {
+        issue(k0, 0);
+        for (int k = k0; k < kend; ++k) {
+            const int s = (k - k0) & 1;
+            const long long base = (long long)k * g.nx * g.ny + (long long)j * g.nx + i;
+            T Fx = F0, Fy = F1, Fz = F2;
+            if (ff) {
+                Fx += __ldg(ff + base);
+                Fy += __ldg(ff + N + base);
+                Fz += __ldg(ff + 2 * N + base);
+            }
+            const T d0 = dJdF[base], d1 = dJdF[N + base], d2 = dJdF[2 * N + base];
+            if (k + 1 < kend) {
+                issue(k + 1, s ^ 1);
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            } else {
+                cp_async_wait_all();
+            }
+            T h[Q], L[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                h[a] = C::load(__uint_as_float(*slot(s, a)), D.w[a], D.iscale[a]);
+                L[a] = __uint_as_float(*slot(s, Q + a));
+            }
+            const RelaxBar<T> rb = collide_vjp<T, CORR>(h, L, P, Fx, Fy, Fz);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) lam_out[(long long)a * N + base] = L[a];
+            dJdF[base] = d0 + rb.Fx;
+            dJdF[N + base] = d1 + rb.Fy;
+            dJdF[2 * N + base] = d2 + rb.Fz;
+            wn_b += (double)rb.wn;
+            wb_b += (double)rb.wb;
+        }
+    }
+    // block sum in fixed order, in the stage memory (no copies are in flight any more)
+    __syncthreads();
+    double *sh = reinterpret_cast<double *>(adj_stage);
+    sh[tid] = wn_b;
+    sh[kAdjThreads + tid] = wb_b;
+    __syncthreads();
+    for (int s = kAdjThreads / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+            sh[tid] += sh[tid + s];
+            sh[kAdjThreads + tid] += sh[kAdjThreads + tid + s];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        wpart[2 * bid] += sh[0];
+        wpart[2 * bid + 1] += sh[kAdjThreads];
+    }
+}
+
 // Per-node VJP of the collision alone for n independent nodes (test entry point):
 // f [27][n] populations, F [3][n], L [27][n] = dJ/df~  ->  fb [27][n] = dJ/df,
 // Fb [3][n], wpart per block (dJ/domega_nu, dJ/domega_xi).

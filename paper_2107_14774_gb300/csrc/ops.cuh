@@ -35,6 +35,10 @@ struct LaunchArgs {
     unsigned sr_key;          // non-zero: stochastic rounding of 16-bit stores with this step key
 };
 
+#ifndef LBC_ADJ_STAGED
+#define LBC_ADJ_STAGED 1   // 4-byte storage: the staged z-marching adjoint (0: one node per thread)
+#endif
+
 #ifndef LBC_PAIR_PLANES
 #define LBC_PAIR_PLANES 1
 #endif
@@ -434,6 +438,33 @@ cudaError_t Ops<ST>::adjoint_step(const LaunchArgs &a, const void *src, const vo
     T *dF = static_cast<T *>(dJdF);
     const Phys<T> P = phys(a);
     const DirConst<T> D = dirs(a);
+    if constexpr (sizeof(S) == 4 && LBC_ADJ_STAGED) {
+        // 4-byte storage: the z-marching adjoint with its state and lambda words staged in
+        // shared memory (same grid in x and y, kAdjPlanes planes per thread)
+        const dim3 mgrid(grid.x, grid.y, (a.g.nz + kAdjPlanes - 1) / kAdjPlanes);
+        // devices on which each kernel's shared-memory attribute is set (bit per device,
+        // one word per correction mode: the three kernels share one function type)
+        static unsigned configured[3] = {0, 0, 0};
+        auto launch = [&](auto kern, int m) -> cudaError_t {
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return e;
+            if (dev >= 32 || !(configured[m] & (1u << dev))) {
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjStageBytes);
+                if (e != cudaSuccess) return e;
+                if (dev < 32) configured[m] |= 1u << dev;
+            }
+            kern<<<mgrid, block, kAdjStageBytes, a.stream>>>(s, li, lo, a.g, P, D, (T)a.F[0], (T)a.F[1], (T)a.F[2], ff,
+                                                             dF, wpart);
+            return cudaGetLastError();
+        };
+        switch (a.corr) {
+        case LB_CORR_NONE: return launch(k_adjoint_march<ST, LB_CORR_NONE>, 0);
+        case LB_CORR_LOWMACH: return launch(k_adjoint_march<ST, LB_CORR_LOWMACH>, 1);
+        case LB_CORR_LOCAL: return launch(k_adjoint_march<ST, LB_CORR_LOCAL>, 2);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.corr) {
     case LB_CORR_NONE:
         k_adjoint<ST, LB_CORR_NONE><<<grid, block, 0, a.stream>>>(s, li, lo, a.g, P, D, (T)a.F[0], (T)a.F[1],
