@@ -21,6 +21,9 @@ CASES = [
     ((24, 10, 13), 0.5, 0.5, "f16s", "y", (2e-6, 0.0, 0.0), "stochastic", "auto", 3),
     ((24, 10, 13), 0.5, 0.5, "bf16s", "", (0.0, 0.0, 0.0), "stochastic", "one", 13),  # one plane per slab
     ((20, 12, 13), 0.5, 2.0, "f64", "y", (1e-5, 0.0, 0.0), "nearest", "auto", 5),
+    # z-marching 16-bit kernel on the slab interiors (plane ranges that start past a ghost plane)
+    ((128, 10, 21), 0.5, 0.5, "bf16s", "", (0.0, 0.0, 0.0), "nearest", "march", 3),
+    ((128, 10, 21), 0.5, 0.5, "f16s", "y", (2e-6, 0.0, 0.0), "stochastic", "march", 4),
 ]
 
 
@@ -89,3 +92,24 @@ def test_subdomains_refuse_force_field():
         lat.set_force_field(torch.zeros(3, 8, 8, 8).cuda())
     assert e.value.status == LB_EINVAL
     lat.close()
+
+
+def test_subdomains_with_lid_changed_between_steps():
+    """A lid at the top y wall whose velocity changes between lb_step calls (lb_set_lid):
+    the decomposed run stores the same bytes as the whole lattice after every call."""
+    from paper_2107_14774_gb300 import Lattice
+    n = (24, 12, 13)
+    rho, u = np.ones(n[::-1]), np.zeros((3,) + n[::-1])
+    out = []
+    for P in (1, 3):
+        lat = Lattice(*n, r_y=0.5, r_z=1.0, nu=0.02, storage="f32", walls="y", lid_u=0.02, subdomains=P,
+                      stream=torch.cuda.Stream())
+        lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+        states = []
+        for lid, k in ((0.02, 3), (0.05, 70), (0.0, 2)):
+            lat.set_lid(lid).step(k)
+            states.append(lat.get_state().cpu())
+        out.append(states)
+        lat.close()
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
