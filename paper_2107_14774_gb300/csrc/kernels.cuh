@@ -438,27 +438,28 @@ k_density_pair(DirPtrs<typename Codec<ST>::S> ptr, Geom g, DirConst<float> D, fl
 // ZC consecutive planes per thread: the loads of plane k+1 are issued before the
 // collision of plane k, so that every warp keeps memory requests in flight while
 // it computes (software pipelining across z).
-// Resident CTAs per SM requested from the compiler.  Five CTAs of 128 threads (at most
-// 102 registers; the compiler takes 96 and spills a few words) hide the load latency
-// better than four at 126 registers: measured on GB300, BF16 storage 35.7 -> 39.8 GLUPS,
-// FP32 on 768-wide rows with y walls 25.2 -> 31.4 GLUPS; six CTAs (80 registers) spill
-// too much.  Without y/z walls the 4-byte forms issue fewer instructions per load and
-// run best at four CTAs (126 registers, no spill): FP32 30.3 -> 32.1 GLUPS on the
-// 512x256x256 decaying flow, while the 2-byte forms keep five (BF16 45.2 vs 41.9).
+// Resident CTAs per SM requested from the compiler.  With walls normal to y or z five
+// CTAs of 128 threads (at most 102 registers; the compiler takes 96 and spills a few
+// words) hide the load latency better than four at 126 registers: measured on GB300,
+// FP32 on 768-wide rows with y walls 25.2 -> 31.4 GLUPS, BF16 and FP16 on that channel
+// 38.2 -> 41.5 and 34.8 -> 38.1.  Without y/z walls the kernel issues fewer instructions
+// per load and runs best at four CTAs (up to 126 registers, no spill): FP32 30.3 -> 32.1
+// GLUPS on the 512x256x256 decaying flow, BF16 45.8 -> 47.6, FP16 44.7 -> 45.1.
+// Stochastic rounding keeps five: at four, BF16 + SR ran 43.2 against 43.6 GLUPS and
+// FP16 + SR 40.1 against 41.5 on the decaying flow.
 #ifndef LBC_PAIR_MINBLOCKS
 #define LBC_PAIR_MINBLOCKS 5
 #endif
 #ifndef LBC_PAIR_SR_MINBLOCKS
-#define LBC_PAIR_SR_MINBLOCKS 5   // stochastic rounding: 33.8 -> 37.7 GLUPS (BF16) at five
+#define LBC_PAIR_SR_MINBLOCKS 5
 #endif
-#ifndef LBC_PAIR_WIDE_PERIODIC_MINBLOCKS
-#define LBC_PAIR_WIDE_PERIODIC_MINBLOCKS 4
+#ifndef LBC_PAIR_PERIODIC_MINBLOCKS
+#define LBC_PAIR_PERIODIC_MINBLOCKS 4
 #endif
 template <int ST, bool SR, bool YZW>
 constexpr int pair_min_blocks()
 {
-    return SR ? LBC_PAIR_SR_MINBLOCKS
-              : ((sizeof(typename Codec<ST>::S) == 4 && !YZW) ? LBC_PAIR_WIDE_PERIODIC_MINBLOCKS : LBC_PAIR_MINBLOCKS);
+    return SR ? LBC_PAIR_SR_MINBLOCKS : (!YZW ? LBC_PAIR_PERIODIC_MINBLOCKS : LBC_PAIR_MINBLOCKS);
 }
 template <int ST, int CORR, int ZC, bool SR, bool YZW>
 __global__ void __launch_bounds__(kBlockThreads, pair_min_blocks<ST, SR, YZW>())
