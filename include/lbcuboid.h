@@ -233,7 +233,9 @@ lb_status lb_objective_ke(lb_ctx *ctx, double *J);
  * (ceil(T/K) + K - 1) stored states of lb_state_bytes each.  K = 1 keeps all T states
  * resident and recomputes nothing (a 128x64x64 FP32 lattice takes 57 MB per state).
  * These work buffers are allocated by the first call that needs them and kept by the
- * context for later calls (grown when a call needs more); lb_destroy frees them.  On return the context holds
+ * context for later calls (grown when a call needs more); lb_destroy frees them.  If
+ * the call returns an error, the context's state is undefined until lb_init,
+ * lb_set_populations or lb_set_state sets it again.  On return the context holds
  * the state after the T steps (as after lb_step(ctx, T)).  Corrections NONE,
  * LOWMACH or LOCAL; no moving lid (LB_EINVAL otherwise).  Synchronises. */
 lb_status lb_adjoint_ke(lb_ctx *ctx, int T, int K, void *dJdF, double dJdomega[2], double *J);
