@@ -21,9 +21,9 @@ EZ = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 
 R, S, CS2 = 0.5, 1.0, 0.08
 
 
-def jacobian(omega_nu, omega_xi, corr):
+def jacobian(omega_nu, omega_xi, corr, r=R, s=S, cs2=CS2):
     """d(post-collision f)/d(pre-collision f) at the rest equilibrium (central differences)."""
-    o = oracle.Oracle(1, 1, 1, r=R, s=S, cs2=CS2, omega_nu=omega_nu, omega_xi=omega_xi, corr=corr)
+    o = oracle.Oracle(1, 1, 1, r=r, s=s, cs2=cs2, omega_nu=omega_nu, omega_xi=omega_xi, corr=corr)
     f0 = o.equilibrium(1.0, (0.0, 0.0, 0.0))
     eps = 1e-7
     cols = []
@@ -34,10 +34,10 @@ def jacobian(omega_nu, omega_xi, corr):
     return np.stack(cols, axis=1)
 
 
-def spectral_radius(omega_nu, omega_xi, corr, nk=12):
+def spectral_radius(omega_nu, omega_xi, corr, nk=12, r=R, s=S, cs2=CS2):
     """Largest |eigenvalue| of the linearised step over an nk^3 grid of wavevectors
     (cell centres of [-pi, pi)^3, so k = 0 and its conserved modes are left out)."""
-    J = jacobian(omega_nu, omega_xi, corr)
+    J = jacobian(omega_nu, omega_xi, corr, r, s, cs2)
     ks = np.linspace(-np.pi, np.pi, nk, endpoint=False) + np.pi / nk
     worst = 0.0
     for kx, ky, kz in itertools.product(ks, ks, ks):
@@ -85,3 +85,21 @@ def test_corrected_rest_state_loses_stability_near_omega_nu_1_9():
     assert spectral_radius(1.9, 1.0, oracle.CORR_LOCAL) < 1.0
     rho = [spectral_radius(1.95, wb, oracle.CORR_LOCAL) for wb in (0.5, 1.0, 1.4)]
     assert min(rho) > 1.005 and rho[0] > rho[1] > rho[2]
+
+
+@pytest.mark.parametrize("cs2", [1.0 / 3.0, 0.08])
+@pytest.mark.parametrize("corr", [oracle.CORR_NONE, oracle.CORR_LOCAL])
+def test_cubic_lattice_rest_stability_does_not_depend_on_omega_xi(corr, cs2):
+    """On the cubic lattice (r = s = 1) the least-damped mode of the rest state is the same for
+    omega_xi = 0.5, 1 and 1.4, with or without the corrections, and stable at omega_nu = 1.98."""
+    rho = [spectral_radius(1.98, wb, corr, r=1.0, s=1.0, cs2=cs2) for wb in (0.5, 1.0, 1.4)]
+    assert max(rho) - min(rho) < 1e-9 and max(rho) < 1.0
+
+
+def test_cuboid_lattice_low_omega_xi_destabilises_the_uncorrected_rest_state():
+    """On the r = 0.5 lattice of Sec. 7 the bulk mode couples to the grid anisotropy: without
+    any corrections the rest state at omega_nu = 1.98 is unstable for omega_xi = 0.5 and
+    stable for omega_xi = 1 and 1.4 -- a larger bulk viscosity destabilises it."""
+    assert spectral_radius(1.98, 0.5, oracle.CORR_NONE) > 1.002
+    assert spectral_radius(1.98, 1.0, oracle.CORR_NONE) < 1.0
+    assert spectral_radius(1.98, 1.4, oracle.CORR_NONE) < 1.0
