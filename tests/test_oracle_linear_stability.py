@@ -21,10 +21,11 @@ EZ = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 
 R, S, CS2 = 0.5, 1.0, 0.08
 
 
-def jacobian(omega_nu, omega_xi, corr, r=R, s=S, cs2=CS2):
-    """d(post-collision f)/d(pre-collision f) at the rest equilibrium (central differences)."""
-    o = oracle.Oracle(1, 1, 1, r=r, s=s, cs2=cs2, omega_nu=omega_nu, omega_xi=omega_xi, corr=corr)
-    f0 = o.equilibrium(1.0, (0.0, 0.0, 0.0))
+def jacobian(omega_nu, omega_xi, corr, r=R, s=S, cs2=CS2, u0=(0.0, 0.0, 0.0), model="central"):
+    """d(post-collision f)/d(pre-collision f) at the equilibrium of density 1 and velocity u0
+    (the rest state by default), by central differences."""
+    o = oracle.Oracle(1, 1, 1, r=r, s=s, cs2=cs2, omega_nu=omega_nu, omega_xi=omega_xi, corr=corr, model=model)
+    f0 = o.equilibrium(1.0, u0)
     eps = 1e-7
     cols = []
     for b in range(27):
@@ -34,10 +35,10 @@ def jacobian(omega_nu, omega_xi, corr, r=R, s=S, cs2=CS2):
     return np.stack(cols, axis=1)
 
 
-def spectral_radius(omega_nu, omega_xi, corr, nk=12, r=R, s=S, cs2=CS2):
+def spectral_radius(omega_nu, omega_xi, corr, nk=12, r=R, s=S, cs2=CS2, u0=(0.0, 0.0, 0.0), model="central"):
     """Largest |eigenvalue| of the linearised step over an nk^3 grid of wavevectors
     (cell centres of [-pi, pi)^3, so k = 0 and its conserved modes are left out)."""
-    J = jacobian(omega_nu, omega_xi, corr, r, s, cs2)
+    J = jacobian(omega_nu, omega_xi, corr, r, s, cs2, u0, model)
     ks = np.linspace(-np.pi, np.pi, nk, endpoint=False) + np.pi / nk
     worst = 0.0
     for kx, ky, kz in itertools.product(ks, ks, ks):
@@ -103,3 +104,13 @@ def test_cuboid_lattice_low_omega_xi_destabilises_the_uncorrected_rest_state():
     assert spectral_radius(1.98, 0.5, oracle.CORR_NONE) > 1.002
     assert spectral_radius(1.98, 1.0, oracle.CORR_NONE) < 1.0
     assert spectral_radius(1.98, 1.4, oracle.CORR_NONE) < 1.0
+
+
+@pytest.mark.parametrize("omega_nu,u", [(1.7, 0.2), (1.8, 0.15)])
+def test_central_moments_stay_stable_in_a_uniform_flow_where_raw_moments_do_not(omega_nu, u):
+    """Sec. 7 (Fig. 8) in linear form: about a uniform flow along x on the r = 0.5 lattice the
+    central-moment scheme (3DCCM) is stable at speeds where the raw-moment scheme (3DCRM) with
+    the same corrected equilibria is not."""
+    central = spectral_radius(omega_nu, 1.0, oracle.CORR_LOCAL, u0=(u, 0.0, 0.0), model="central")
+    raw = spectral_radius(omega_nu, 1.0, oracle.CORR_LOCAL, u0=(u, 0.0, 0.0), model="raw")
+    assert central < 1.0 < raw
